@@ -1,0 +1,235 @@
+"""FP64 CPU oracle of the curved-space lattice Boltzmann method (arXiv 1803.07822).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py`` -- never by the library.  It shares
+no code with the CUDA path; see ``cslbm_oracle.c`` for the method as written
+from the paper (literal f-form, Sec. II; geometry, App. A; Hermite
+expansion, App. B; lattice gradient, App. D; transformation, Sec. IV.B).
+
+Parity unpinned (no printed value to match; held only by convergence and
+invariant tests): the boundary-node rule and the transformation variants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cslbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PERIODIC, WALL, INFLOW, OUTFLOW = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off, so x86 and Arm agree)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            for name in ("orc_geometry", "orc_init", "orc_step", "orc_fill_boundary",
+                         "orc_moments", "orc_mass", "orc_wall_force", "orc_transform",
+                         "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
+                         "orc_lattice"):
+                getattr(_lib, name).restype = ctypes.c_int
+    return _lib
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
+                ("tau", ctypes.c_double), ("theta", ctypes.c_double),
+                ("fext", ctypes.c_double * 3), ("literal_a2", ctypes.c_int)]
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def lattice():
+    """(c [19,3] int, w [19]) as the oracle defines them."""
+    lib = _load()
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19)
+    lib.orc_lattice(_p(c), _p(w))
+    return c.reshape(19, 3), w
+
+
+def geometry(n, g6, dg18):
+    """g_ij, d_k g_ij -> (sqrt g [N], g^ij [9,N], Gamma^i_jk [27,N])."""
+    lib = _load()
+    N = int(np.prod(n))
+    g6 = _f64(g6, (6, N))
+    dg18 = _f64(dg18, (18, N))
+    sg = np.zeros(N)
+    gi = np.zeros((9, N))
+    gam = np.zeros((27, N))
+    nn = (ctypes.c_int * 3)(*n)
+    if lib.orc_geometry(nn, _p(g6), _p(dg18), _p(sg), _p(gi), _p(gam)) != 0:
+        raise ValueError("metric not positive definite")
+    return sg, gi, gam
+
+
+def feq(rho, j3, ginv9, sqrtg, theta=1.0 / 3.0):
+    lib = _load()
+    j3 = _f64(j3)
+    gi = _f64(ginv9)
+    out = np.zeros(19)
+    lib.orc_feq(ctypes.c_double(rho), _p(j3), _p(gi), ctypes.c_double(sqrtg),
+                ctypes.c_double(theta), _p(out))
+    return out
+
+
+def forcing_recompose(A, B3, C9, sqrtg):
+    lib = _load()
+    B3 = _f64(B3)
+    C9 = _f64(C9)
+    out = np.zeros(19)
+    lib.orc_forcing_recompose(ctypes.c_double(A), _p(B3), _p(C9), ctypes.c_double(sqrtg), _p(out))
+    return out
+
+
+def forcing_moments(j3, T9, Dj9, ginv9, gam27, theta=1.0 / 3.0, fext3=(0, 0, 0)):
+    """A, B^i, C^ij (Eqs. forcing-A/B/C) for one node; Dj9[k*3+i] = d_k(rho u^i)."""
+    lib = _load()
+    args = [_f64(x) for x in (j3, T9, Dj9, ginv9, gam27)]
+    fe = _f64(fext3)
+    A = ctypes.c_double(0.0)
+    B = np.zeros(3)
+    C = np.zeros(9)
+    lib.orc_forcing_moments(*[_p(a) for a in args], ctypes.c_double(theta), _p(fe),
+                            ctypes.byref(A), _p(B), _p(C))
+    return A.value, B, C
+
+
+class Lattice:
+    """One channel advanced by the oracle.
+
+    n = (n0, n1, n2), axis 0 fastest; bc_lo/bc_hi per axis in
+    {PERIODIC, WALL, INFLOW, OUTFLOW}; fext is the contravariant body force
+    density (constant); theta defaults to c_s^2 = 1/3.
+    """
+
+    def __init__(self, n, bc_lo=(0, 0, 0), bc_hi=None, tau=0.8, theta=1.0 / 3.0,
+                 fext=(0.0, 0.0, 0.0), literal_a2=False):
+        self.lib = _load()
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        bc_hi = bc_lo if bc_hi is None else bc_hi
+        self.params = _Params((ctypes.c_int * 3)(*self.n), (ctypes.c_int * 3)(*bc_lo),
+                              (ctypes.c_int * 3)(*bc_hi), float(tau), float(theta),
+                              (ctypes.c_double * 3)(*fext), int(bool(literal_a2)))
+        self.f = np.zeros((19, self.N))
+        self.Fprev = np.zeros((19, self.N))
+        self.sqrtg = np.ones(self.N)
+        gi = np.zeros((9, self.N))
+        gi[[0, 4, 8]] = 1.0
+        self.ginv = gi
+        self.gam = np.zeros((27, self.N))
+        self._faces = [None] * 6
+        self._face_ptrs = (ctypes.c_void_p * 6)()
+
+    # -- geometry and boundary data ------------------------------------
+    def set_metric(self, g6, dg18):
+        self.sqrtg, self.ginv, self.gam = geometry(self.n, g6, dg18)
+
+    def face_shape(self, axis):
+        o = sorted(((axis + 1) % 3, (axis + 2) % 3))
+        return self.n[o[0]] * self.n[o[1]]
+
+    def set_face_velocity(self, axis, side, u3):
+        """Contravariant velocity [3, face nodes] imposed on face (axis, side)."""
+        k = axis * 2 + side
+        if u3 is None:
+            self._faces[k] = None
+            self._face_ptrs[k] = None
+        else:
+            a = _f64(u3, (3, self.face_shape(axis)))
+            self._faces[k] = a
+            self._face_ptrs[k] = a.ctypes.data
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise ValueError(f"oracle {what} failed ({rc})")
+
+    # -- method ---------------------------------------------------------
+    def init(self, rho0=None, u0=None):
+        rho0 = np.ones(self.N) if rho0 is None else _f64(rho0, (self.N,))
+        u0 = np.zeros((3, self.N)) if u0 is None else _f64(u0, (3, self.N))
+        self._check(self.lib.orc_init(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv),
+                                      _p(self.gam), _p(rho0), _p(u0), self._face_ptrs,
+                                      _p(self.f), _p(self.Fprev)), "init")
+
+    def step(self, nsteps=1):
+        self._check(self.lib.orc_step(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv),
+                                      _p(self.gam), self._face_ptrs, _p(self.f), _p(self.Fprev),
+                                      ctypes.c_int(nsteps)), "step")
+
+    def filled(self):
+        fb = np.zeros_like(self.f)
+        self._check(self.lib.orc_fill_boundary(ctypes.byref(self.params), _p(self.sqrtg),
+                                               _p(self.ginv), self._face_ptrs, _p(self.f),
+                                               _p(fb)), "fill")
+        return fb
+
+    def moments(self, J9=None):
+        """(rho [N], u [3,N]) -- contravariant, or Cartesian v = J u with J9."""
+        rho = np.zeros(self.N)
+        u = np.zeros((3, self.N))
+        Jkeep = None if J9 is None else _f64(J9, (9, self.N))
+        Jp = None if Jkeep is None else _p(Jkeep)
+        self._check(self.lib.orc_moments(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv),
+                                         self._face_ptrs, _p(self.f), Jp, _p(rho), _p(u)),
+                    "moments")
+        return rho, u
+
+    def mass(self):
+        m = ctypes.c_double(0.0)
+        self._check(self.lib.orc_mass(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv),
+                                      self._face_ptrs, _p(self.f), ctypes.byref(m)), "mass")
+        return m.value
+
+    def wall_force(self, axis, side, J9):
+        J = _f64(J9, (9, self.N))
+        out = np.zeros(3)
+        self._check(self.lib.orc_wall_force(ctypes.byref(self.params), _p(self.sqrtg),
+                                            _p(self.ginv), self._face_ptrs, _p(self.f), _p(J),
+                                            ctypes.c_int(axis), ctypes.c_int(side), _p(out)),
+                    "wall_force")
+        return out
+
+    def transform(self, g6_new, dg18_new, Jold9, Jnew9):
+        """Chart change (Sec. IV.B): transform f and the forcing history, then
+        adopt the new geometry."""
+        sg_new, gi_new, gam_new = geometry(self.n, g6_new, dg18_new)
+        Jo = _f64(Jold9, (9, self.N))
+        Jn = _f64(Jnew9, (9, self.N))
+        self._check(self.lib.orc_transform(ctypes.byref(self.params), _p(self.sqrtg),
+                                           _p(self.ginv), _p(sg_new), _p(Jo), _p(Jn),
+                                           self._face_ptrs, _p(self.f), _p(self.Fprev)),
+                    "transform")
+        self.sqrtg, self.ginv, self.gam = sg_new, gi_new, gam_new

@@ -1,0 +1,698 @@
+/*
+ * cslbm_oracle.c -- plain FP64 CPU oracle of the curved-space lattice Boltzmann
+ * step of Flouris et al., "Fluid structure interaction with curved space
+ * lattice Boltzmann" (arXiv 1803.07822).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header or table with the CUDA
+ * library: the D3Q19 set, the Hermite recomposition, the forcing moments and
+ * the boundary rules are written out here a second time, from the paper.
+ *
+ * It runs the method in its literal f-form: collision (Eq. collision, Sec. II)
+ * then streaming (Eq. streaming, Sec. II), the forcing history F(x,t-dt) kept
+ * as 19 values per node, every tensor contraction written out from the full
+ * Christoffel tensor.  Plain loops, FP64, no blocking or fusion; the node
+ * loops carry an OpenMP pragma and nothing else.
+ *
+ * Layouts (all structure-of-arrays, axis 0 fastest):
+ *   node   = x + n0*(y + n1*z)
+ *   f      [19][N]        distribution f_lambda(x,t) as streamed (raw: the
+ *                         populations a boundary node receives from outside
+ *                         the domain are NaN until the boundary rule fills them)
+ *   Fprev  [19][N]        F_lambda(x, t - dt)
+ *   g6     [6][N]         g_00,g_01,g_02,g_11,g_12,g_22
+ *   dg18   [18][N]        d_k g_ij at (k*6 + ij), ij in the order of g6
+ *   sqrtg  [N], ginv [9][N] (full 3x3), gam [27][N] Gamma^i_jk at (i*9+j*3+k)
+ *   J9     [9][N]         J^a_i = d h^a / d x^i at (a*3 + i)
+ *   face velocity (axis a, side s): [3][face nodes], face node = the two other
+ *                         coordinates in increasing axis order, lower fastest;
+ *                         contravariant components; NULL means zero.
+ *
+ * Readings of points the paper leaves open (each documented in the design
+ * notes of the repository): D3Q19 textbook weights, theta = c_s^2, Hermite
+ * truncation at second order, the collision with its leading f, the textbook
+ * Christoffel formula, F(x,-dt) := F(x,0), boundary nodes defined by
+ * non-equilibrium extrapolation from the node one step inward along every
+ * non-periodic face normal, linear ghost extrapolation for the gradient
+ * stencil, wall force = s * sum J T^{in} sqrt(g).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 19
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
+
+typedef struct {
+    int n[3];
+    int bc_lo[3], bc_hi[3];
+    double tau, theta;
+    double fext[3];
+    int literal_a2; /* transform a_(2) itself as a tensor instead of Pi */
+} orc_params;
+
+/* D3Q19: rest, six faces, twelve edges (Fig. lb_velocities, Sec. II). */
+static const int CV[Q][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double wgt(int l)
+{
+    int s = abs(CV[l][0]) + abs(CV[l][1]) + abs(CV[l][2]);
+    return s == 0 ? 1.0 / 3.0 : (s == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+static const double CS2 = 1.0 / 3.0; /* c_s^2 */
+
+static long nodes(const orc_params *p) { return (long)p->n[0] * p->n[1] * p->n[2]; }
+
+static long idx(const orc_params *p, int x, int y, int z)
+{
+    return x + (long)p->n[0] * (y + (long)p->n[1] * z);
+}
+
+static void coords(const orc_params *p, long i, int r[3])
+{
+    r[0] = (int)(i % p->n[0]);
+    r[1] = (int)((i / p->n[0]) % p->n[1]);
+    r[2] = (int)(i / ((long)p->n[0] * p->n[1]));
+}
+
+int orc_lattice(int *c57, double *w19)
+{
+    for (int l = 0; l < Q; l++) {
+        for (int a = 0; a < 3; a++) c57[l * 3 + a] = CV[l][a];
+        w19[l] = wgt(l);
+    }
+    return Q;
+}
+
+/* ------------------------------------------------------------------ */
+/* Geometry: metric -> inverse metric, sqrt(g), Christoffel symbols     */
+/* (App. A: g_ij, g^ij, Gamma^i_jk = 1/2 g^il (d_j g_kl + d_k g_jl - d_l g_jk)) */
+/* ------------------------------------------------------------------ */
+static int sym6(int i, int j)
+{
+    static const int m[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    return m[i][j];
+}
+
+int orc_geometry(const int n[3], const double *g6, const double *dg18,
+                 double *sqrtg, double *ginv9, double *gam27)
+{
+    long N = (long)n[0] * n[1] * n[2];
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad)
+    for (long v = 0; v < N; v++) {
+        double g[3][3], gi[3][3], dg[3][3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                g[i][j] = g6[sym6(i, j) * N + v];
+                for (int k = 0; k < 3; k++) dg[k][i][j] = dg18[(k * 6 + sym6(i, j)) * N + v];
+            }
+        /* inverse by cofactors */
+        double det = g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1])
+                   - g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0])
+                   + g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+        if (!(det > 0.0)) { bad = 1; continue; }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+                gi[i][j] = (g[r0][c0] * g[r1][c1] - g[r0][c1] * g[r1][c0]) / det;
+            }
+        sqrtg[v] = sqrt(det);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) ginv9[(i * 3 + j) * N + v] = gi[i][j];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                for (int k = 0; k < 3; k++) {
+                    double s = 0.0;
+                    for (int l = 0; l < 3; l++)
+                        s += gi[i][l] * (dg[j][k][l] + dg[k][j][l] - dg[l][j][k]);
+                    gam27[(i * 9 + j * 3 + k) * N + v] = 0.5 * s;
+                }
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Hermite expansions (Eq. expansion-equilibrium-distribution, App. B)  */
+/* ------------------------------------------------------------------ */
+
+/* f_l = w_l/sqrt(g) * sum_n 1/(n! c_s^n) a_(n) : H_(n), n <= 2, with
+ * H_(0) = 1, H_(1) = c/c_s, H_(2) = c c / c_s^2 - delta.                    */
+static double hermite_recompose(int l, double sg, double a0, const double a1[3],
+                                const double a2[3][3])
+{
+    double cs = sqrt(CS2), h1 = 0.0, h2 = 0.0;
+    for (int i = 0; i < 3; i++) {
+        h1 += a1[i] * (CV[l][i] / cs);
+        for (int j = 0; j < 3; j++)
+            h2 += a2[i][j] * (CV[l][i] * CV[l][j] / CS2 - (i == j ? 1.0 : 0.0));
+    }
+    return wgt(l) / sg * (a0 + h1 / cs + h2 / (2.0 * CS2));
+}
+
+/* f^eq with a0 = rho, a1 = rho u, a2 = rho(theta g^ij - c_s^2 delta) + rho u u
+ * (App. B, coefficients of the equilibrium).                                 */
+static void feq_node(double rho, const double j[3], const double gi[3][3], double sg,
+                     double theta, double out[Q])
+{
+    double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho}, a2[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++)
+            a2[a][b] = rho * (theta * gi[a][b] - CS2 * (a == b)) + rho * u[a] * u[b];
+    for (int l = 0; l < Q; l++) out[l] = hermite_recompose(l, sg, rho, j, a2);
+}
+
+/* F_l from b_(0) = A, b_(1) = B, b_(2) = C - c_s^2 delta A (Eq. forcing2).   */
+static void forcing_node(double A, const double B[3], const double C[3][3], double sg,
+                         double out[Q])
+{
+    double b2[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) b2[a][b] = C[a][b] - CS2 * (a == b) * A;
+    for (int l = 0; l < Q; l++) out[l] = hermite_recompose(l, sg, A, B, b2);
+}
+
+/* exported single-node versions for the identity tests */
+int orc_feq(double rho, const double *j3, const double *ginv9, double sg, double theta,
+            double *out19)
+{
+    double gi[3][3];
+    for (int a = 0; a < 9; a++) gi[a / 3][a % 3] = ginv9[a];
+    feq_node(rho, j3, gi, sg, theta, out19);
+    return 0;
+}
+
+int orc_forcing_recompose(double A, const double *B3, const double *C9, double sg,
+                          double *out19)
+{
+    double C[3][3];
+    for (int a = 0; a < 9; a++) C[a / 3][a % 3] = C9[a];
+    forcing_node(A, B3, C, sg, out19);
+    return 0;
+}
+
+/* Forcing moments A, B^i, C^ij of Eqs. forcing-A, forcing-B, forcing-C.
+ *   j  = rho u^i, T = T^ij, Dj[k][i] = d_k (rho u^i), gi = g^ij, gam = Gamma.
+ * Written from the full Christoffel tensor, each contraction as printed.     */
+static void forcing_moments(const double j[3], const double T[3][3], const double Dj[3][3],
+                            const double gi[3][3], const double gam[3][3][3], double theta,
+                            const double fext[3], double *A, double B[3], double C[3][3])
+{
+    double a = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 3; k++) a -= gam[i][i][k] * j[k] + gam[k][i][k] * j[i];
+    *A = a;
+
+    for (int i = 0; i < 3; i++) {
+        double b = fext[i];
+        for (int jj = 0; jj < 3; jj++)
+            for (int k = 0; k < 3; k++)
+                b -= gam[k][jj][k] * T[i][jj] + gam[i][jj][k] * T[jj][k] + gam[jj][jj][k] * T[k][i];
+        B[i] = b;
+    }
+
+    /* bar-d_k (rho u^i) = d_k(rho u^i) - Gamma^l_kl rho u^i;
+     * nabla_k (rho u^i) = d_k(rho u^i) + Gamma^i_kl rho u^l                     */
+    double bard[3][3], cov[3][3];
+    for (int k = 0; k < 3; k++) {
+        double trace = gam[0][k][0] + gam[1][k][1] + gam[2][k][2];
+        for (int i = 0; i < 3; i++) {
+            bard[k][i] = Dj[k][i] - trace * j[i];
+            double s = Dj[k][i];
+            for (int l = 0; l < 3; l++) s += gam[i][k][l] * j[l];
+            cov[k][i] = s;
+        }
+    }
+    double divbar = bard[0][0] + bard[1][1] + bard[2][2];
+    double divcov = cov[0][0] + cov[1][1] + cov[2][2];
+    for (int i = 0; i < 3; i++)
+        for (int jj = 0; jj < 3; jj++) {
+            double s = CS2 * (bard[jj][i] + bard[i][jj] + (i == jj ? divbar : 0.0));
+            for (int k = 0; k < 3; k++) s -= theta * (cov[k][i] * gi[jj][k] + cov[k][jj] * gi[i][k]);
+            s -= theta * divcov * gi[i][jj];
+            C[i][jj] = s;
+        }
+}
+
+int orc_forcing_moments(const double *j3, const double *T9, const double *Dj9,
+                        const double *ginv9, const double *gam27, double theta,
+                        const double *fext3, double *A, double *B3, double *C9)
+{
+    double T[3][3], Dj[3][3], gi[3][3], gam[3][3][3], C[3][3];
+    for (int a = 0; a < 9; a++) {
+        T[a / 3][a % 3] = T9[a];
+        Dj[a / 3][a % 3] = Dj9[a];
+        gi[a / 3][a % 3] = ginv9[a];
+    }
+    for (int a = 0; a < 27; a++) gam[a / 9][(a / 3) % 3][a % 3] = gam27[a];
+    forcing_moments(j3, T, Dj, gi, gam, theta, fext3, A, B3, C);
+    for (int a = 0; a < 9; a++) C9[a] = C[a / 3][a % 3];
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-node helpers on whole fields                                     */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const double *sqrtg, *ginv, *gam;
+} geom_t;
+
+static void load_geom(const geom_t *G, long N, long v, double *sg, double gi[3][3],
+                      double gam[3][3][3])
+{
+    *sg = G->sqrtg[v];
+    for (int a = 0; a < 9; a++) gi[a / 3][a % 3] = G->ginv[a * N + v];
+    if (gam)
+        for (int a = 0; a < 27; a++) gam[a / 9][(a / 3) % 3][a % 3] = G->gam[a * N + v];
+}
+
+/* rho = sum f sqrt g, rho u^i = sum f c^i sqrt g, Pi^ij = sum f c^i c^j sqrt g
+ * (Eqs. fields1, fields2, fields3).                                        */
+static void moments(const double *f, long N, long v, double sg, double *rho, double j[3],
+                    double Pi[3][3])
+{
+    double r = 0.0, m[3] = {0, 0, 0}, P[3][3] = {{0}};
+    for (int l = 0; l < Q; l++) {
+        double fl = f[l * N + v] * sg;
+        r += fl;
+        for (int a = 0; a < 3; a++) {
+            m[a] += fl * CV[l][a];
+            for (int b = 0; b < 3; b++) P[a][b] += fl * CV[l][a] * CV[l][b];
+        }
+    }
+    *rho = r;
+    for (int a = 0; a < 3; a++) {
+        j[a] = m[a];
+        if (Pi)
+            for (int b = 0; b < 3; b++) Pi[a][b] = P[a][b];
+    }
+}
+
+/* Boundary classification: a node on one or more non-periodic faces takes its
+ * rule from the face of highest priority (wall > inflow > outflow; ties by
+ * axis, lower side first).  Its inner node is the node one step inward along
+ * the normal of every non-periodic face it lies on.                          */
+static int classify(const orc_params *p, const int r[3], int *axis, int *side, int inner[3])
+{
+    int best = 0, rank = 0;
+    static const int prio[4] = {0, 3, 2, 1};
+    for (int a = 0; a < 3; a++) inner[a] = r[a];
+    for (int a = 0; a < 3; a++) {
+        for (int s = 0; s < 2; s++) {
+            int bc = s ? p->bc_hi[a] : p->bc_lo[a];
+            if (bc == BC_PERIODIC) continue;
+            int on = s ? (r[a] == p->n[a] - 1) : (r[a] == 0);
+            if (!on) continue;
+            inner[a] = s ? r[a] - 1 : r[a] + 1;
+            if (prio[bc] > rank) {
+                rank = prio[bc];
+                best = bc;
+                *axis = a;
+                *side = s;
+            }
+        }
+    }
+    return best;
+}
+
+static long face_index(const orc_params *p, int axis, const int r[3])
+{
+    int a = (axis + 1) % 3, b = (axis + 2) % 3;
+    if (a > b) { int t = a; a = b; b = t; }
+    return r[a] + (long)p->n[a] * r[b];
+}
+
+/* Boundary rule (Sec. V.A, open boundaries by extrapolation, no-slip by a
+ * fixed velocity on the boundary node): non-equilibrium extrapolation for
+ * wall and inflow nodes, zero-gradient copy for outflow nodes, both scaled by
+ * sqrt(g_inner)/sqrt(g_node) so that sqrt(g)-weighted moments carry over.   */
+static void apply_bc(const orc_params *p, const geom_t *G, const double *const *uface,
+                     const double *fin, double *fout)
+{
+    long N = nodes(p);
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        int r[3], in[3], axis = 0, side = 0;
+        coords(p, v, r);
+        int bc = classify(p, r, &axis, &side, in);
+        if (bc == BC_PERIODIC) {
+            if (fin != fout)
+                for (int l = 0; l < Q; l++) fout[l * N + v] = fin[l * N + v];
+            continue;
+        }
+        long vi = idx(p, in[0], in[1], in[2]);
+        double sgw, giw[3][3], sgi, gii[3][3];
+        load_geom(G, N, v, &sgw, giw, NULL);
+        load_geom(G, N, vi, &sgi, gii, NULL);
+        if (bc == BC_OUTFLOW) {
+            for (int l = 0; l < Q; l++) fout[l * N + v] = fin[l * N + vi] * sgi / sgw;
+            continue;
+        }
+        double rho, j[3], uw[3] = {0, 0, 0}, jw[3], fe_w[Q], fe_i[Q];
+        moments(fin, N, vi, sgi, &rho, j, NULL);
+        const double *uf = uface[axis * 2 + side];
+        if (uf) {
+            long fi = face_index(p, axis, r);
+            int nf = p->n[(axis + 1) % 3] * p->n[(axis + 2) % 3];
+            for (int a = 0; a < 3; a++) uw[a] = uf[a * (long)nf + fi];
+        }
+        for (int a = 0; a < 3; a++) jw[a] = rho * uw[a];
+        feq_node(rho, jw, giw, sgw, p->theta, fe_w);
+        feq_node(rho, j, gii, sgi, p->theta, fe_i);
+        for (int l = 0; l < Q; l++)
+            fout[l * N + v] = fe_w[l] + (fin[l * N + vi] - fe_i[l]) * sgi / sgw;
+    }
+}
+
+/* momentum field value at a possibly out-of-range site: periodic axes wrap,
+ * a site one step outside a non-periodic face takes the linear extrapolation
+ * 2 j(face) - j(face - normal), applied axis by axis.                        */
+static double jval(const orc_params *p, const double *jf, long N, int comp, int x, int y, int z)
+{
+    int r[3] = {x, y, z};
+    for (int a = 0; a < 3; a++) {
+        int periodic = (r[a] < 0 ? p->bc_lo[a] : p->bc_hi[a]) == BC_PERIODIC;
+        if (r[a] >= 0 && r[a] < p->n[a]) continue;
+        if (periodic) {
+            r[a] = (r[a] + p->n[a]) % p->n[a];
+            continue;
+        }
+        int r0[3] = {r[0], r[1], r[2]}, r1[3] = {r[0], r[1], r[2]};
+        if (r[a] < 0) { r0[a] = 0; r1[a] = 1; }
+        else { r0[a] = p->n[a] - 1; r1[a] = p->n[a] - 2; }
+        return 2.0 * jval(p, jf, N, comp, r0[0], r0[1], r0[2])
+             - jval(p, jf, N, comp, r1[0], r1[1], r1[2]);
+    }
+    return jf[comp * N + idx(p, r[0], r[1], r[2])];
+}
+
+/* Forcing field F(x,t) of the boundary-filled state fb, plus f^eq (Eq.
+ * forcing2 with A, B, C of Eqs. forcing-A/B/C; T of Eq. fields3; the lattice
+ * gradient of App. D:  d_k phi = 1/(c_s^2 dt) sum_l w_l c_l^k phi(x + c_l)). */
+static void forcing_field(const orc_params *p, const geom_t *G, const double *fb,
+                          double *F, double *feq)
+{
+    long N = nodes(p);
+    double *jf = (double *)malloc(sizeof(double) * 3 * N);
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        double rho, j[3];
+        moments(fb, N, v, G->sqrtg[v], &rho, j, NULL);
+        for (int a = 0; a < 3; a++) jf[a * N + v] = j[a];
+    }
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        int r[3];
+        coords(p, v, r);
+        double sg, gi[3][3], gam[3][3][3], rho, j[3], Pi[3][3], fe[Q];
+        load_geom(G, N, v, &sg, gi, gam);
+        moments(fb, N, v, sg, &rho, j, Pi);
+        feq_node(rho, j, gi, sg, p->theta, fe);
+        /* T = sum f^eq c c sqrt g + (1 - 1/2tau) sum (f - f^eq) c c sqrt g */
+        double T[3][3] = {{0}};
+        for (int l = 0; l < Q; l++) {
+            double fl = fb[l * N + v];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++)
+                    T[a][b] += (fe[l] + (1.0 - 0.5 / p->tau) * (fl - fe[l])) * CV[l][a] * CV[l][b] * sg;
+        }
+        double Dj[3][3] = {{0}};
+        for (int l = 1; l < Q; l++) {
+            for (int i = 0; i < 3; i++) {
+                double jn = jval(p, jf, N, i, r[0] + CV[l][0], r[1] + CV[l][1], r[2] + CV[l][2]);
+                for (int k = 0; k < 3; k++) Dj[k][i] += wgt(l) * CV[l][k] * jn / CS2;
+            }
+        }
+        double A, B[3], C[3][3], Fl[Q];
+        forcing_moments(j, T, Dj, gi, gam, p->theta, p->fext, &A, B, C);
+        forcing_node(A, B, C, sg, Fl);
+        for (int l = 0; l < Q; l++) {
+            F[l * N + v] = Fl[l];
+            if (feq) feq[l * N + v] = fe[l];
+        }
+    }
+    free(jf);
+}
+
+static int check_params(const orc_params *p)
+{
+    for (int a = 0; a < 3; a++) {
+        if (p->n[a] < 1) return -1;
+        if ((p->bc_lo[a] == BC_PERIODIC) != (p->bc_hi[a] == BC_PERIODIC)) return -1;
+        if (p->bc_lo[a] != BC_PERIODIC && p->n[a] < 3) return -1;
+    }
+    if (!(p->tau > 0.5)) return -1;
+    return 0;
+}
+
+/* Initial state: f = f^eq(rho0, u0; g) and F(x, -dt) := F(x, 0), the forcing
+ * of that state (its boundary nodes filled by the boundary rule).           */
+int orc_init(const orc_params *p, const double *sqrtg, const double *ginv9, const double *gam27,
+             const double *rho0, const double *u0, const double *const *uface, double *f,
+             double *Fprev)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    geom_t G = {sqrtg, ginv9, gam27};
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        double sg, gi[3][3], j[3], fe[Q];
+        load_geom(&G, N, v, &sg, gi, NULL);
+        for (int a = 0; a < 3; a++) j[a] = rho0[v] * u0[a * N + v];
+        feq_node(rho0[v], j, gi, sg, p->theta, fe);
+        for (int l = 0; l < Q; l++) f[l * N + v] = fe[l];
+    }
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    apply_bc(p, &G, uface, f, fb);
+    forcing_field(p, &G, fb, Fprev, NULL);
+    free(fb);
+    return 0;
+}
+
+/* nsteps of the curved-space LB equation (Eq. CE-LB) split as
+ *   f*(x,t)      = f - (f - f^eq)/tau + F(x,t) - 1/2 F(x,t-dt)   (collision)
+ *   f(x,t+dt)    = f*(x - c dt, t) + 1/2 F(x,t)                  (streaming)
+ * with the boundary rule applied to f(t) before the moments are taken.      */
+int orc_step(const orc_params *p, const double *sqrtg, const double *ginv9, const double *gam27,
+             const double *const *uface, double *f, double *Fprev, int nsteps)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    geom_t G = {sqrtg, ginv9, gam27};
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    double *F = (double *)malloc(sizeof(double) * Q * N);
+    double *fe = (double *)malloc(sizeof(double) * Q * N);
+    double *fs = (double *)malloc(sizeof(double) * Q * N);
+    double om = 1.0 / p->tau;
+    for (int t = 0; t < nsteps; t++) {
+        apply_bc(p, &G, uface, f, fb);
+        forcing_field(p, &G, fb, F, fe);
+#pragma omp parallel for
+        for (long q = 0; q < (long)Q * N; q++)
+            fs[q] = fb[q] - om * (fb[q] - fe[q]) + F[q] - 0.5 * Fprev[q];
+#pragma omp parallel for
+        for (long v = 0; v < N; v++) {
+            int r[3];
+            coords(p, v, r);
+            for (int l = 0; l < Q; l++) {
+                int s[3], inside = 1;
+                for (int a = 0; a < 3; a++) {
+                    s[a] = r[a] - CV[l][a];
+                    if (s[a] < 0 || s[a] >= p->n[a]) {
+                        int bc = s[a] < 0 ? p->bc_lo[a] : p->bc_hi[a];
+                        if (bc == BC_PERIODIC) s[a] = (s[a] + p->n[a]) % p->n[a];
+                        else inside = 0;
+                    }
+                }
+                f[l * N + v] = inside ? fs[l * N + idx(p, s[0], s[1], s[2])] + 0.5 * F[l * N + v] : NAN;
+            }
+        }
+        memcpy(Fprev, F, sizeof(double) * Q * N);
+    }
+    free(fb);
+    free(F);
+    free(fe);
+    free(fs);
+    return 0;
+}
+
+/* Boundary-filled copy of the state (what every reader of f sees).          */
+int orc_fill_boundary(const orc_params *p, const double *sqrtg, const double *ginv9,
+                      const double *const *uface, const double *f, double *fb)
+{
+    if (check_params(p)) return -1;
+    geom_t G = {sqrtg, ginv9, NULL};
+    apply_bc(p, &G, uface, f, fb);
+    return 0;
+}
+
+/* rho, u^i = rho u^i / rho (Eqs. fields1/2); with J9 the Cartesian velocity
+ * v^a = J^a_i u^i (Eq. vector_transform read from Q to C).                  */
+int orc_moments(const orc_params *p, const double *sqrtg, const double *ginv9,
+                const double *const *uface, const double *f, const double *J9, double *rho,
+                double *u3)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    orc_fill_boundary(p, sqrtg, ginv9, uface, f, fb);
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        double r, j[3], u[3];
+        moments(fb, N, v, sqrtg[v], &r, j, NULL);
+        for (int a = 0; a < 3; a++) u[a] = j[a] / r;
+        rho[v] = r;
+        for (int a = 0; a < 3; a++) {
+            double s = u[a];
+            if (J9) {
+                s = 0.0;
+                for (int i = 0; i < 3; i++) s += J9[(a * 3 + i) * N + v] * u[i];
+            }
+            u3[a * N + v] = s;
+        }
+    }
+    free(fb);
+    return 0;
+}
+
+/* Total mass M = sum_x sqrt(g) rho (volume element sqrt(g) d^3x, App. A).   */
+int orc_mass(const orc_params *p, const double *sqrtg, const double *ginv9,
+             const double *const *uface, const double *f, double *out)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    orc_fill_boundary(p, sqrtg, ginv9, uface, f, fb);
+    double m = 0.0;
+    for (long v = 0; v < N; v++) {
+        double r, j[3];
+        moments(fb, N, v, sqrtg[v], &r, j, NULL);
+        m += sqrtg[v] * r;
+    }
+    free(fb);
+    *out = m;
+    return 0;
+}
+
+/* Force of the fluid on the face (axis, side): with the covariant area
+ * element sqrt(g) dx dx of a coordinate plane,
+ *   F^a = s * sum_{wall nodes} J^a_i T^{i axis} sqrt(g),  s = -1 low, +1 high,
+ * T of Eq. fields3 from the boundary-filled populations (Sec. IV.A force
+ * coupling: T_net . n on the nodes).                                         */
+int orc_wall_force(const orc_params *p, const double *sqrtg, const double *ginv9,
+                   const double *const *uface, const double *f, const double *J9, int axis,
+                   int side, double *out3)
+{
+    if (check_params(p) || axis < 0 || axis > 2) return -1;
+    long N = nodes(p);
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    orc_fill_boundary(p, sqrtg, ginv9, uface, f, fb);
+    geom_t G = {sqrtg, ginv9, NULL};
+    double acc[3] = {0, 0, 0}, s = side ? 1.0 : -1.0;
+    int plane = side ? p->n[axis] - 1 : 0;
+    for (long v = 0; v < N; v++) {
+        int r[3];
+        coords(p, v, r);
+        if (r[axis] != plane) continue;
+        double sg, gi[3][3], rho, j[3], fe[Q], T[3][3] = {{0}};
+        load_geom(&G, N, v, &sg, gi, NULL);
+        moments(fb, N, v, sg, &rho, j, NULL);
+        feq_node(rho, j, gi, sg, p->theta, fe);
+        for (int l = 0; l < Q; l++) {
+            double fl = fb[l * N + v];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++)
+                    T[a][b] += (fe[l] + (1.0 - 0.5 / p->tau) * (fl - fe[l])) * CV[l][a] * CV[l][b] * sg;
+        }
+        for (int a = 0; a < 3; a++)
+            for (int i = 0; i < 3; i++) acc[a] += s * J9[(a * 3 + i) * N + v] * T[i][axis] * sg;
+    }
+    free(fb);
+    for (int a = 0; a < 3; a++) out3[a] = acc[a];
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Transformation of f and of the forcing history under a chart change  */
+/* (Sec. IV.B): moments a_(0), a_(1), a_(2) transformed as tensors with  */
+/* D phi = Jnew^-1 Jold at each node, then recomposed with the new       */
+/* sqrt(g) to second order.                                              */
+/* ------------------------------------------------------------------ */
+static void inv3(const double m[3][3], double o[3][3])
+{
+    double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1])
+               - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+               + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+            o[i][j] = (m[r0][c0] * m[r1][c1] - m[r0][c1] * m[r1][c0]) / det;
+        }
+}
+
+/* a -> D a,  M -> D M D^T */
+static void tensor_transform(const double D[3][3], const double a1[3], const double M[3][3],
+                             double o1[3], double oM[3][3])
+{
+    for (int i = 0; i < 3; i++) {
+        o1[i] = 0.0;
+        for (int l = 0; l < 3; l++) o1[i] += D[i][l] * a1[l];
+    }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0.0;
+            for (int l = 0; l < 3; l++)
+                for (int m = 0; m < 3; m++) s += D[i][l] * D[j][m] * M[l][m];
+            oM[i][j] = s;
+        }
+}
+
+int orc_transform(const orc_params *p, const double *sqrtg_old, const double *ginv9_old,
+                  const double *sqrtg_new, const double *Jold9, const double *Jnew9,
+                  const double *const *uface, double *f, double *Fprev)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    orc_fill_boundary(p, sqrtg_old, ginv9_old, uface, f, fb);
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        double Jo[3][3], Jn[3][3], Jni[3][3], D[3][3];
+        for (int a = 0; a < 9; a++) {
+            Jo[a / 3][a % 3] = Jold9[a * N + v];
+            Jn[a / 3][a % 3] = Jnew9[a * N + v];
+        }
+        inv3(Jn, Jni);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                D[i][j] = 0.0;
+                for (int k = 0; k < 3; k++) D[i][j] += Jni[i][k] * Jo[k][j];
+            }
+        double so = sqrtg_old[v], sn = sqrtg_new[v];
+        for (int pass = 0; pass < 2; pass++) {
+            /* pass 0: f, pass 1: forcing history */
+            double *src = pass ? Fprev : fb;
+            double *dst = pass ? Fprev : f;
+            double a0, a1[3], M[3][3];
+            moments(src, N, v, so, &a0, a1, M);
+            if (p->literal_a2) /* a_(2) = sum f (c c - c_s^2 delta) sqrt g */
+                for (int i = 0; i < 3; i++) M[i][i] -= CS2 * a0;
+            double t1[3], tM[3][3], t2[3][3];
+            tensor_transform(D, a1, M, t1, tM);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    t2[i][j] = tM[i][j] - (p->literal_a2 ? 0.0 : CS2 * a0 * (i == j));
+            for (int l = 0; l < Q; l++) dst[l * N + v] = hermite_recompose(l, sn, a0, t1, t2);
+        }
+    }
+    free(fb);
+    return 0;
+}

@@ -1,0 +1,271 @@
+"""Seeded synthetic inputs: charts, metrics, boundary velocities, body forces.
+
+This module serves both the CUDA path and the CPU oracle.  It holds no step of
+the lattice Boltzmann method: it only plays the part of the caller -- the FEM
+shell of the paper, which is out of scope -- that hands the solver a chart
+h(x) and the metric it induces.  All geometry is analytic and FP64.
+
+Conventions: a field on an (n0, n1, n2) lattice is an array [components, N]
+with node = x + n0*(y + n1*z) (axis 0 fastest).  J9[a*3+i] = d h^a / d x^i.
+g6 holds g_00, g_01, g_02, g_11, g_12, g_22; dg18[k*6+ij] = d_k g_ij.
+
+Channel layout used by all workloads: axis 0 is wall-normal (walls at
+x = 0 and x = n0-1; the x = 0 wall is fixed), axis 1 is the span (periodic),
+axis 2 is the flow direction.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SYM = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def grid(n):
+    """Coordinate arrays (x, y, z), each [N], in node order."""
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return x.ravel().astype(np.float64), y.ravel().astype(np.float64), z.ravel().astype(np.float64)
+
+
+@dataclass
+class Chart:
+    """A chart h: lattice -> Cartesian space, given by its first and second
+    derivatives at the nodes, with the metric it induces (g = J^T J)."""
+    n: tuple
+    J9: np.ndarray          # [9, N]
+    hess: np.ndarray        # [27, N]  d_j d_k h^a at (a*9 + j*3 + k)
+    g6: np.ndarray = field(init=False)
+    dg18: np.ndarray = field(init=False)
+
+    def __post_init__(self):
+        N = self.J9.shape[1]
+        J = self.J9.reshape(3, 3, N)            # [a, i]
+        Hs = self.hess.reshape(3, 3, 3, N)      # [a, j, k]
+        g = np.einsum("ain,ajn->ijn", J, J)
+        dg = np.einsum("akin,ajn->kijn", Hs, J) + np.einsum("ain,akjn->kijn", J, Hs)
+        self.g6 = np.stack([g[i, j] for i, j in SYM])
+        self.dg18 = np.stack([dg[k, i, j] for k in range(3) for i, j in SYM])
+
+    @property
+    def N(self):
+        return self.J9.shape[1]
+
+
+def flat_chart(n):
+    N = int(np.prod(n))
+    J9 = np.zeros((9, N))
+    J9[[0, 4, 8]] = 1.0
+    return Chart(tuple(n), J9, np.zeros((27, N)))
+
+
+def reparam_chart(n, eps):
+    """Pure re-parametrisation of a flat channel across axis 0:
+    x_c = x + eps * L/pi * sin(pi x / L), L = n0 - 1 (end points fixed).
+    Space stays flat; only the coordinates are stretched."""
+    x, _, _ = grid(n)
+    L = n[0] - 1
+    N = x.size
+    J9 = np.zeros((9, N))
+    J9[0] = 1.0 + eps * np.cos(np.pi * x / L)
+    J9[4] = 1.0
+    J9[8] = 1.0
+    hess = np.zeros((27, N))
+    hess[0] = -eps * (np.pi / L) * np.sin(np.pi * x / L)
+    return Chart(tuple(n), J9, hess)
+
+
+def reparam_position(n, eps):
+    """Cartesian wall-normal coordinate x_c(x) of the nodes of reparam_chart."""
+    x, _, _ = grid(n)
+    L = n[0] - 1
+    return x + eps * L / np.pi * np.sin(np.pi * x / L)
+
+
+@dataclass
+class Deformation:
+    """Wall displacement d(p, s) of the top wall and its derivatives, per node
+    (the same value for every wall-normal index)."""
+    d: np.ndarray
+    dp: np.ndarray
+    ds: np.ndarray
+    dpp: np.ndarray
+    dps: np.ndarray
+    dss: np.ndarray
+
+    def scaled(self, a):
+        return Deformation(*(a * v for v in (self.d, self.dp, self.ds, self.dpp, self.dps, self.dss)))
+
+
+def fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, kmax=4, lmax=3,
+                        coeffs=None, modes=None):
+    """d = amp * H * D / max|D| with D = sum_m c_m cos(2 pi k_m s/L_s + 2 pi l_m p/L_p + phi_m);
+    on a non-periodic flow axis d is tapered by sin^2(pi s/(n2-1)) so that the
+    inlet and outlet stay flat.  c_m ~ N(0,1), k_m in 1..kmax, l_m in 0..lmax,
+    phi_m ~ U[0, 2 pi), all from numpy's default_rng(seed).  When ``coeffs`` and
+    ``modes`` are given they replace the draws (``amp`` is then an absolute
+    scale: d = amp * H * D)."""
+    _, p, s = grid(n)
+    H = n[0] - 1
+    Ls = n[2] if flow_periodic else n[2] - 1
+    Lp = n[1]
+    if modes is None:
+        rng = np.random.default_rng(seed)
+        k = rng.integers(1, kmax + 1, size=n_modes)
+        l = rng.integers(0, lmax + 1, size=n_modes)
+        c = rng.standard_normal(n_modes)
+        phi = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    else:
+        k, l, phi = (np.asarray(v, dtype=np.float64) for v in modes)
+        c = np.asarray(coeffs, dtype=np.float64)
+    D = np.zeros_like(s)
+    Dp, Ds, Dpp, Dps, Dss = (np.zeros_like(s) for _ in range(5))
+    for m in range(len(c)):
+        ks = 2.0 * np.pi * k[m] / Ls
+        lp = 2.0 * np.pi * l[m] / Lp
+        th = ks * s + lp * p + phi[m]
+        cth, sth = np.cos(th), np.sin(th)
+        D += c[m] * cth
+        Ds -= c[m] * ks * sth
+        Dp -= c[m] * lp * sth
+        Dss -= c[m] * ks * ks * cth
+        Dpp -= c[m] * lp * lp * cth
+        Dps -= c[m] * ks * lp * cth
+    K = amp * H / np.max(np.abs(D)) if modes is None else amp * H
+    if flow_periodic:
+        S, S1, S2 = np.ones_like(s), np.zeros_like(s), np.zeros_like(s)
+    else:
+        w = np.pi / (n[2] - 1)
+        S = np.sin(w * s) ** 2
+        S1 = w * np.sin(2.0 * w * s)
+        S2 = 2.0 * w * w * np.cos(2.0 * w * s)
+    return Deformation(K * D * S, K * Dp * S, K * (Ds * S + D * S1), K * Dpp * S,
+                       K * (Dps * S + Dp * S1), K * (Dss * S + 2.0 * Ds * S1 + D * S2))
+
+
+def channel_chart(n, dfm: Deformation):
+    """Exterior linear interpolation between the fixed wall x = 0 and the
+    displaced wall x = H (Sec. IV.A position coupling, case (i)):
+    h(x, p, s) = (x (1 + d(p,s)/H), p, s)."""
+    x, _, _ = grid(n)
+    H = n[0] - 1
+    N = x.size
+    J9 = np.zeros((9, N))
+    J9[0] = 1.0 + dfm.d / H
+    J9[1] = x * dfm.dp / H
+    J9[2] = x * dfm.ds / H
+    J9[4] = 1.0
+    J9[8] = 1.0
+    hess = np.zeros((27, N))
+    # d_j d_k h^0
+    hess[0 * 9 + 0 * 3 + 1] = hess[0 * 9 + 1 * 3 + 0] = dfm.dp / H
+    hess[0 * 9 + 0 * 3 + 2] = hess[0 * 9 + 2 * 3 + 0] = dfm.ds / H
+    hess[0 * 9 + 1 * 3 + 1] = x * dfm.dpp / H
+    hess[0 * 9 + 1 * 3 + 2] = hess[0 * 9 + 2 * 3 + 1] = x * dfm.dps / H
+    hess[0 * 9 + 2 * 3 + 2] = x * dfm.dss / H
+    return Chart(tuple(n), J9, hess)
+
+
+def face_nodes(n, axis, side):
+    """Node indices of face (axis, side) in face order (the other two axes,
+    lower axis fastest)."""
+    x, y, z = grid(n)
+    r = (x, y, z)
+    sel = r[axis] == (n[axis] - 1 if side else 0)
+    return np.nonzero(sel)[0]
+
+
+def contravariant(J9, v3, nodes):
+    """u = J^-1 v at the given nodes (Eq. vector_transform from C to Q)."""
+    J = J9[:, nodes].T.reshape(-1, 3, 3)
+    return np.linalg.solve(J, v3.T[..., None])[..., 0].T
+
+
+def wall_velocity(n, chart: Chart, dfm_rate: Deformation):
+    """Contravariant velocity of the top wall (x = n0-1) moving with d'(t):
+    Cartesian v = (dd/dt, 0, 0), u = J^-1 v."""
+    nodes = face_nodes(n, 0, 1)
+    v = np.zeros((3, nodes.size))
+    v[0] = dfm_rate.d[nodes]
+    return contravariant(chart.J9, v, nodes)
+
+
+def inflow_profile(n, chart: Chart, umax):
+    """Parabolic inflow on face (axis 2, low): Cartesian v_flow =
+    4 umax xc (H - xc) / H^2 with xc the Cartesian wall-normal position."""
+    nodes = face_nodes(n, 2, 0)
+    x, _, _ = grid(n)
+    H = n[0] - 1
+    xc = x[nodes] * chart.J9[0, nodes]  # h^0 = x (1 + d/H) and J^0_0 = 1 + d/H
+    v = np.zeros((3, nodes.size))
+    v[2] = 4.0 * umax * xc * (H - xc) / (H * H)
+    return contravariant(chart.J9, v, nodes)
+
+
+def body_force(nu, umax, H):
+    """Poiseuille drive: |F| = 8 nu umax / H^2 (centre-line speed umax)."""
+    return 8.0 * nu * umax / (H * H)
+
+
+def random_spd_metric(rng, eps=0.2):
+    """A random symmetric positive-definite 3x3 metric near the identity."""
+    A = np.eye(3) + eps * rng.standard_normal((3, 3))
+    return A.T @ A
+
+
+def time_law(t, period=2000.0):
+    """Amplitude factor a(t) = sin^2(pi t / period) and its rate."""
+    w = np.pi / period
+    return np.sin(w * t) ** 2, w * np.sin(2.0 * w * t)
+
+
+# --------------------------------------------------------------------------
+# Workloads.  Each returns a dict with: n, bc_lo, bc_hi, tau, fext, chart and,
+# where relevant, the deformation generator and the face velocities.
+# --------------------------------------------------------------------------
+WALL, PERIODIC, INFLOW, OUTFLOW = 1, 0, 2, 3
+
+
+def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None):
+    """Walls across axis 0, periodic span and flow, body-force drive along
+    axis 2 with centre-line speed umax."""
+    nu = (tau - 0.5) / 3.0
+    H = n[0] - 1
+    dfm = fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, modes=modes,
+                              coeffs=coeffs)
+    return dict(n=tuple(n), bc_lo=(WALL, PERIODIC, PERIODIC), bc_hi=(WALL, PERIODIC, PERIODIC),
+                tau=tau, fext=(0.0, 0.0, body_force(nu, umax, H)), dfm=dfm,
+                chart=channel_chart(n, dfm), faces={})
+
+
+def plain_fp64_channel(n=(16, 16, 32)):
+    """Static one-mode channel: d = 0.05 H sin(2 pi s / n2), tau = 0.8,
+    body force for umax = 0.05 (the first workload of the plain method)."""
+    return periodic_channel(n, 0.8, 0.05, 1, 0.05, 0, modes=([1], [0], [-np.pi / 2]),
+                            coeffs=[1.0])
+
+
+def dynamic_channel(n=(128, 128, 256), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
+                    t=0.0, period=2000.0):
+    """Walls across axis 0, periodic span, parabolic inflow at z = 0 and
+    outflow at z = n2-1; deformation scaled by a(t) = sin^2(pi t/period)."""
+    nu = (tau - 0.5) / 3.0
+    H = n[0] - 1
+    umax = re * nu / H
+    base = fourier_deformation(n, n_modes, amp, seed, flow_periodic=False)
+    a, adot = time_law(t, period)
+    dfm = base.scaled(a)
+    chart = channel_chart(n, dfm)
+    faces = {(2, 0): inflow_profile(n, chart, umax), (0, 1): wall_velocity(n, chart, base.scaled(adot))}
+    return dict(n=tuple(n), bc_lo=(WALL, PERIODIC, INFLOW), bc_hi=(WALL, PERIODIC, OUTFLOW),
+                tau=tau, fext=(0.0, 0.0, 0.0), dfm=dfm, base=base, chart=chart, faces=faces,
+                umax=umax, period=period)
+
+
+def dynamic_channel_at(w, t):
+    """The chart and face velocities of a dynamic_channel workload at time t."""
+    a, adot = time_law(t, w["period"])
+    chart = channel_chart(w["n"], w["base"].scaled(a))
+    faces = {(2, 0): inflow_profile(w["n"], chart, w["umax"]),
+             (0, 1): wall_velocity(w["n"], chart, w["base"].scaled(adot))}
+    return chart, faces
