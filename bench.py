@@ -1,0 +1,350 @@
+"""Throughput benchmark of the curved-space LBM hot path on GB300.
+
+Workload (default): the dynamic deformed channel -- 128 x 128 x 256 nodes,
+walls across axis 0, periodic span, parabolic inflow / outflow along the flow
+axis, tau = 0.6 (Re ~ 100), a 16-mode seeded wall deformation of 10 %
+amplitude under the time law sin^2(pi t / 2000), FP32 storage.  One bench
+step is one cycle of that schedule: metric update + transformation of f
+(every 10 LBM steps), 10 LBM steps, then the FP64 mass and wall-force
+reductions.  Metric snapshots are generated up front (the caller's job) and
+cycled.  MLUPS = lattice nodes x LBM steps / time.
+
+Inputs (1.4 GB of state per LBM step) exceed the 129 MB L2, so no flush is
+needed between timed iterations.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 every rank advances its own channel (independent problems, weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1803_07822_gb300 import inputs as I  # noqa: E402
+
+METRIC = "curved-space LBM MLUPS and HBM GB/s vs peak; adjoint/forward step-time ratio"
+UNIT = "MLUPS"
+STEPS_PER_CYCLE = 10
+# algorithmic bytes per node update: 19 f read + 19 written, 10 history
+# coefficients read + written (FP32), 25 geometry values read (FP32)
+BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 + 80 + 100,
+                  "bf16": 19 * 2 * 2 + 80 + 100, "fp64": 19 * 8 * 2 + 80 + 100}
+
+
+def workload_spec(name):
+    if name == "dynamic":
+        return dict(n=(128, 128, 256), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
+                    storage="fp32", label="deformed channel 128x128x256, dynamic metric (16 modes, 10 %), "
+                                          "inflow/outflow, tau 0.6, Re 100, FP32, transform every 10 steps")
+    if name == "crop64":
+        return dict(n=(64, 64, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0, storage="fp32",
+                    label="deformed channel 64x64x128 (profiling case), dynamic metric, inflow/outflow, FP32")
+    if name == "target256":
+        return dict(n=(256, 256, 256), seed=3000, n_modes=8, amp=0.08, tau=0.6, re=100.0, storage="fp32",
+                    label="deformed channel 256^3, dynamic metric (8 modes, 8 %), inflow/outflow, tau 0.6, FP32")
+    raise ValueError(name)
+
+
+def snapshots(w, times):
+    out = []
+    for t in times:
+        ch, faces = I.dynamic_channel_at(w, t)
+        out.append((ch, faces))
+    return out
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].strip() == "Active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_cycle_sample(spec, steps, warm):
+    """The FP64 oracle on a bounded sample of the same workload: the same
+    generator on a 1/8-volume crop (half the extent per axis), timed over
+    whole cycles (metric transform + 10 steps).  Returns (MLUPS, seconds,
+    nodes, cores)."""
+    import oracle
+    n = tuple(v // 2 for v in spec["n"])
+    w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
+                          re=spec["re"])
+    snaps = snapshots(w, [500.0 + STEPS_PER_CYCLE * k for k in range(steps + warm + 1)])
+    o = oracle.Lattice(n, w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+    ch0, f0 = snaps[0]
+    o.set_metric(ch0.g6, ch0.dg18)
+    for (a, s), u in f0.items():
+        o.set_face_velocity(a, s, u)
+    o.init()
+    prev = ch0
+    t_total = 0.0
+    for k in range(1, steps + warm + 1):
+        ch, faces = snaps[k]
+        t0 = time.perf_counter()
+        o.transform(ch.g6, ch.dg18, prev.J9, ch.J9)
+        for (a, s), u in faces.items():
+            o.set_face_velocity(a, s, u)
+        o.step(STEPS_PER_CYCLE)
+        o.mass()
+        o.wall_force(0, 1, ch.J9)
+        dt = time.perf_counter() - t0
+        prev = ch
+        if k > warm:
+            t_total += dt
+    N = int(np.prod(n))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return N * STEPS_PER_CYCLE * steps / t_total / 1e6, t_total, n, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = workload_spec(args.workload)
+    mlups, secs, n, cores = oracle_cycle_sample(spec, args.steps, args.warmup)
+    sample = (f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, {args.steps} timed cycles "
+              f"({STEPS_PER_CYCLE} steps + transform + reductions each), FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec["label"], "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
+    ap.add_argument("--workload", default="dynamic", choices=["dynamic", "target256", "crop64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--snapshots", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+
+    rank, world, local = dist_setup(args)
+    spec = workload_spec(args.workload)
+    w = I.dynamic_channel(n=spec["n"], seed=spec["seed"] + rank, n_modes=spec["n_modes"], amp=spec["amp"],
+                          tau=spec["tau"], re=spec["re"])
+    N = int(np.prod(spec["n"]))
+    times = [500.0 + STEPS_PER_CYCLE * k for k in range(args.snapshots + 1)]
+    snaps = snapshots(w, times)
+    lat = CurvedLattice(spec["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=spec["storage"])
+    # device-resident inputs for the kernel-throughput run
+    dev = []
+    for ch, faces in snaps:
+        d = {k: torch.as_tensor(getattr(ch, k), device="cuda") for k in ("g6", "dg18", "J9")}
+        d["faces"] = {key: torch.as_tensor(u, device="cuda") for key, u in faces.items()}
+        dev.append(d)
+    ch0, faces0 = snaps[0]
+    lat.set_chart(ch0)
+    for (a, s), u in faces0.items():
+        lat.set_boundary_velocity(a, s, u)
+    lat.init_equilibrium()
+
+    def cycle_dev(k):
+        d = dev[1 + k % args.snapshots]
+        lat.update_metric(d["g6"], d["dg18"], d["J9"])
+        for (a, s), u in d["faces"].items():
+            lat.set_boundary_velocity(a, s, u)
+        lat.step(STEPS_PER_CYCLE)
+        lat.total_mass()
+        lat.wall_force(0, 1)
+
+    for k in range(args.warmup):
+        cycle_dev(k)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    lat.profile(True)
+    stream = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        cycle_dev(args.warmup + k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    step_ms_total, nprof, launches = lat.profile_read()
+    lat.profile(False)
+    ms = reduce_max(ms, world)
+    ok = lat.check()
+    ms_per_step = ms / args.steps
+    value = world * N * STEPS_PER_CYCLE * args.steps / (ms * 1e-3) / 1e6
+
+    peak, peak_kind = peaks()
+    step_ms = step_ms_total / max(nprof, 1)
+    bpn = BYTES_PER_NODE[spec["storage"]]
+    achieved = bpn * N / (step_ms * 1e-3) / 1e9
+    e2e = None if args.no_e2e else end_to_end(args, lat, snaps, N, world)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if spec["storage"] == "fp32" else spec["storage"], "data": "synthetic",
+        "config": {"workload": spec["label"], "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
+                   "l2": "inputs > L2 (1.4 GB of state per LBM step), no flush",
+                   "state_finite_after_run": ok},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_step_fused (one launch per LBM step)", "bytes_per_node": bpn,
+                     "step_ms": step_ms},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, secs, n, cores = oracle_cycle_sample(spec, 2, 0)
+        line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, 2 cycles "
+                                          f"(transform + {STEPS_PER_CYCLE} steps + reductions), FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def end_to_end(args, lat, snaps, N, world):
+    """The same cycles through the public API with pinned host buffers: the
+    metric inputs and face velocities are copied host -> device and the mass
+    and wall force read back inside the timed region."""
+    import torch
+    pinned = []
+    h2d = 0
+    for ch, faces in snaps:
+        p = {}
+        for k in ("g6", "dg18", "J9"):
+            t = torch.empty(getattr(ch, k).shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = getattr(ch, k)
+            p[k] = t.numpy()
+        p["faces"] = {}
+        for key, u in faces.items():
+            t = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = u
+            p["faces"][key] = t.numpy()
+        pinned.append(p)
+    h2d = sum(pinned[1][k].nbytes for k in ("g6", "dg18", "J9")) + sum(u.nbytes for u in pinned[1]["faces"].values())
+    d2h = 4 * 8
+
+    def cycle_host(k):
+        p = pinned[1 + k % args.snapshots]
+        lat.update_metric(p["g6"], p["dg18"], p["J9"])
+        for (a, s), u in p["faces"].items():
+            lat.set_boundary_velocity(a, s, u)
+        lat.step(STEPS_PER_CYCLE)
+        lat.total_mass()
+        lat.wall_force(0, 1)
+
+    for k in range(2):
+        cycle_host(k)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        cycle_host(k)
+    torch.cuda.synchronize()
+    t_e2e = reduce_max(time.perf_counter() - t0, world)
+    barrier(world)
+    return {"value": world * N * STEPS_PER_CYCLE * args.steps / t_e2e / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * cslbm.h -- C ABI of the GB300 curved-space lattice Boltzmann library
+ * (the method of Flouris et al., "Fluid structure interaction with curved
+ * space lattice Boltzmann", arXiv 1803.07822).
+ *
+ * One channel (a regular D3Q19 lattice carrying a metric field) lives in a
+ * context.  Every device buffer belongs to the caller: the library asks how
+ * many bytes it needs (cslbm_workspace_bytes), the caller allocates them (e.g.
+ * as a torch tensor) and hands them to cslbm_create.  The library never calls
+ * cudaMalloc or cudaFree.  The context itself is a small host object.
+ *
+ * Conventions shared by every entry point
+ *   - lattice n = (n0, n1, n2); node = x + n0*(y + n1*z) (axis 0 fastest);
+ *     N = n0*n1*n2.  Lattice units: dx = dt = 1.
+ *   - fields are structure-of-arrays: component c of node v at [c*N + v].
+ *   - g6 [6][N] FP64: g_00, g_01, g_02, g_11, g_12, g_22 (the metric g_ij).
+ *   - dg18 [18][N] FP64: d_k g_ij at row k*6 + ij, ij in the order of g6.
+ *   - J9 [9][N] FP64: the chart's Jacobian J^a_i = d h^a / d x^i at row a*3+i.
+ *   - a face (axis a, side s) holds the nodes with x_a = 0 (s = 0) or
+ *     x_a = n_a - 1 (s = 1); its nodes are ordered by the two other axes,
+ *     lower axis fastest.
+ *   - `on_device` != 0: pointers are device memory on the context's device;
+ *     0: pointers are host memory (pinned memory is fastest); the library
+ *     copies through a staging area inside the workspace.
+ *   - All work is enqueued on the context's stream.  Entry points that return
+ *     a host value (mass, wall force, host-buffer readout) synchronise that
+ *     stream before returning.
+ *   - Errors: every entry point returns a cslbm_status; the message of the
+ *     last failure on the calling thread is returned by cslbm_last_error().
+ *     A failing call leaves the context usable unless it returns CSLBM_ECUDA.
+ */
+#ifndef CSLBM_H
+#define CSLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CSLBM_OK = 0,
+    CSLBM_EINVAL = 1,    /* bad argument (sizes, axes, null pointers, tau <= 1/2) */
+    CSLBM_ECUDA = 2,     /* a CUDA call failed; the message names it */
+    CSLBM_ENOMEM = 3,    /* workspace smaller than cslbm_workspace_bytes */
+    CSLBM_EUNSTABLE = 4, /* non-finite density or velocity found by cslbm_check */
+    CSLBM_ETIMEOUT = 5,  /* reserved: a bounded device wait expired */
+    CSLBM_ESTATE = 6     /* call out of order (e.g. step before init) */
+} cslbm_status;
+
+/* Storage of the distributions.  All variants store f - w_lambda (weight
+ * shifted); FP32/FP16/BF16 compute in FP32, FP64 computes in FP64. */
+typedef enum { CSLBM_FP32 = 0, CSLBM_FP16S = 1, CSLBM_BF16S = 2, CSLBM_FP64 = 3 } cslbm_storage;
+
+/* Face rules (Sec. V.A: no-slip by a fixed velocity on the boundary node,
+ * open boundaries by extrapolation from the inner neighbours).  A node on
+ * several non-periodic faces follows WALL over INFLOW over OUTFLOW, ties by
+ * axis then low side first. */
+typedef enum { CSLBM_PERIODIC = 0, CSLBM_WALL = 1, CSLBM_INFLOW = 2, CSLBM_OUTFLOW = 3 } cslbm_bc;
+
+typedef struct {
+    int n[3];           /* nodes per axis; >= 3 on non-periodic axes */
+    int bc_lo[3];       /* cslbm_bc of the low face of each axis */
+    int bc_hi[3];       /* ... of the high face; periodic on both or neither */
+    double tau;         /* BGK relaxation time (Eq. CE-LB), > 1/2 */
+    double theta;       /* normalised temperature (App. B); <= 0 selects c_s^2 = 1/3 */
+    double fext[3];     /* body-force density, contravariant, constant (Eq. forcing-B) */
+    int storage;        /* cslbm_storage */
+    int transform_flags;/* bit 0: transform a_(2) itself instead of the momentum flux Pi */
+} cslbm_params;
+
+typedef struct cslbm_ctx cslbm_ctx;
+
+/* Bytes of device workspace a context with these parameters needs. */
+cslbm_status cslbm_workspace_bytes(const cslbm_params* p, size_t* bytes);
+
+/* Create a context on the current CUDA device.  `workspace` is caller-owned
+ * device memory of at least cslbm_workspace_bytes (256-byte aligned), kept
+ * alive until cslbm_destroy; `stream` is a cudaStream_t (NULL = legacy
+ * default stream).  The metric starts flat (g = delta, J = I). */
+cslbm_status cslbm_create(const cslbm_params* p, void* workspace, size_t bytes, void* stream,
+                          cslbm_ctx** out);
+
+/* Release the host context; never touches the caller's device memory. */
+cslbm_status cslbm_destroy(cslbm_ctx* ctx);
+
+/* Metric update kernel (App. A): from g_ij and d_k g_ij compute, per node and
+ * in FP64, the inverse metric g^ij, sqrt(g) = sqrt(det g_ij) and
+ *   Gamma^i_jk = 1/2 g^il (d_j g_kl + d_k g_jl - d_l g_jk),
+ * stored in the compute precision.  No transformation of f: use before
+ * cslbm_init_equilibrium or for a static metric.  EINVAL if det g <= 0
+ * anywhere (checked on the device, reported after a sync). */
+cslbm_status cslbm_set_metric(cslbm_ctx* ctx, const double* g6, const double* dg18, int on_device);
+
+/* Set the chart Jacobian J9 used for Cartesian readout, wall forces and the
+ * next chart change.  No transformation of f. */
+cslbm_status cslbm_set_jacobian(cslbm_ctx* ctx, const double* J9, int on_device);
+
+/* Chart change (Sec. IV.B): the metric update of cslbm_set_metric for the new
+ * chart, then the distributions and the forcing history are transformed node
+ * by node with D phi = Jnew^-1 Jold (Jold = the current Jacobian): a_(0) kept,
+ * a_(1) -> D phi a_(1), Pi -> D phi Pi D phi^T (or a_(2) itself, see
+ * transform_flags), recomposed to second order with the new sqrt(g).  The
+ * history's A, B, C transform as scalar, vector and rank-2 tensor.  Jnew
+ * becomes the current Jacobian. */
+cslbm_status cslbm_update_metric(cslbm_ctx* ctx, const double* g6, const double* dg18,
+                                 const double* Jnew9, int on_device);
+
+/* Initial state f = f^eq(rho, u; g) (App. B) with the boundary rule on the
+ * boundary nodes, and forcing history F(x,-dt) := F(x,0).  rho [N] and
+ * u3 [3][N] (contravariant) are FP64; NULL selects rho = 1 / u = 0. */
+cslbm_status cslbm_init_equilibrium(cslbm_ctx* ctx, const double* rho, const double* u3,
+                                    int on_device);
+
+/* Velocity imposed on the nodes of a WALL or INFLOW face (Sec. IV.A velocity
+ * coupling): u3 [3][face nodes] FP64, contravariant.  NULL sets zero.
+ * EINVAL for a periodic or outflow face. */
+cslbm_status cslbm_set_boundary_velocity(cslbm_ctx* ctx, int axis, int side, const double* u3,
+                                         int on_device);
+
+/* Advance nsteps of the curved-space LB equation (Eq. CE-LB) split into
+ * collision (Eq. collision) and streaming (Eq. streaming), with the Hermite
+ * equilibrium (App. B), the forcing of Eqs. forcing2 / forcing-A/B/C with the
+ * trapezoidal history, the isotropic lattice gradient of App. D and the
+ * boundary rule.  Asynchronous. */
+cslbm_status cslbm_step(cslbm_ctx* ctx, int nsteps);
+
+/* Density and velocity (Eqs. fields1/2): rho [N], u3 [3][N], FP64;
+ * contravariant u^i, or Cartesian v^a = J^a_i u^i when cartesian != 0. */
+cslbm_status cslbm_get_moments(cslbm_ctx* ctx, double* rho, double* u3, int cartesian,
+                               int on_device);
+
+/* Total mass sum_x sqrt(g) rho (volume element of App. A), FP64. Syncs. */
+cslbm_status cslbm_total_mass(cslbm_ctx* ctx, double* out);
+
+/* Force of the fluid on the face (axis, side), Cartesian, FP64 (Sec. IV.A
+ * force coupling):  F^a = s sum_nodes J^a_i T^{i axis} sqrt(g), s = -1 for
+ * the low face and +1 for the high face, T of Eq. fields3. Syncs. */
+cslbm_status cslbm_wall_force(cslbm_ctx* ctx, int axis, int side, double out3[3]);
+
+/* Non-finite or supersonic (|u|^2 g > 0.3^2 in lattice units) state?
+ * Returns CSLBM_EUNSTABLE if so, CSLBM_OK otherwise. Syncs. */
+cslbm_status cslbm_check(cslbm_ctx* ctx);
+
+/* Checkpoint: the bytes of the evolving state (distributions + forcing
+ * history), copied to/from `buf` (device or host per on_device). */
+cslbm_status cslbm_state_bytes(const cslbm_ctx* ctx, size_t* bytes);
+cslbm_status cslbm_save_state(cslbm_ctx* ctx, void* buf, size_t bytes, int on_device);
+cslbm_status cslbm_load_state(cslbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
+
+/* Profiling.  While enabled, each LBM step enqueued by cslbm_step is
+ * bracketed by CUDA events on the context's stream and every kernel launch
+ * of the library is counted.  Enabling resets the counters. */
+cslbm_status cslbm_profile_enable(cslbm_ctx* ctx, int enable);
+
+/* Sum of the event-timed durations of the profiled LBM steps (ms), their
+ * number, and the kernel launches counted since profiling was enabled.
+ * Synchronises the stream. */
+cslbm_status cslbm_profile_read(cslbm_ctx* ctx, double* step_ms, long long* nsteps, long long* launches);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* cslbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSLBM_H */

@@ -1,0 +1,514 @@
+// C ABI of the curved-space lattice Boltzmann library: context, workspace
+// layout, host<->device staging and the order of kernel launches.  The
+// kernels themselves live in kernels.cuh (one instantiation per format).
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ctx.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+cslbm_status fail(cslbm_status s, const std::string& m)
+{
+    g_err = m;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(CSLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCH_CHECK(what)                                                                          \
+    do {                                                                                            \
+        cudaError_t e_ = cudaGetLastError();                                                        \
+        if (e_ != cudaSuccess) return fail(CSLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr long long kMaxChunk = 1LL << 20;  // nodes per host-transfer chunk
+constexpr int kStagingDoubles = 24;           // per node: g6 + dg18
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t off_P[2], off_H[2], off_G[2], off_J, off_jf, off_face[6], off_scratch, off_staging, total;
+    size_t s_bytes, r_bytes;
+    long long N, chunk, face_n[6];
+};
+
+const cslbm_ops* ops_for(int storage)
+{
+    switch (storage) {
+    case CSLBM_FP32: return &cslbm_ops_fp32;
+    case CSLBM_FP16S: return &cslbm_ops_fp16;
+    case CSLBM_BF16S: return &cslbm_ops_bf16;
+    case CSLBM_FP64: return &cslbm_ops_fp64;
+    default: return nullptr;
+    }
+}
+
+cslbm_status validate(const cslbm_params* p)
+{
+    if (!p) return fail(CSLBM_EINVAL, "params is null");
+    for (int a = 0; a < 3; a++) {
+        if (p->n[a] < 1) return fail(CSLBM_EINVAL, "n must be >= 1 on every axis");
+        for (int s = 0; s < 2; s++) {
+            int b = s ? p->bc_hi[a] : p->bc_lo[a];
+            if (b < CSLBM_PERIODIC || b > CSLBM_OUTFLOW) return fail(CSLBM_EINVAL, "unknown boundary rule");
+        }
+        if ((p->bc_lo[a] == CSLBM_PERIODIC) != (p->bc_hi[a] == CSLBM_PERIODIC))
+            return fail(CSLBM_EINVAL, "an axis is periodic on both faces or on neither");
+        if (p->bc_lo[a] != CSLBM_PERIODIC && p->n[a] < 3)
+            return fail(CSLBM_EINVAL, "a non-periodic axis needs at least 3 nodes");
+    }
+    if (!(p->tau > 0.5)) return fail(CSLBM_EINVAL, "tau must exceed 1/2");
+    if (!ops_for(p->storage)) return fail(CSLBM_EINVAL, "unknown storage format");
+    if ((long long)p->n[0] * p->n[1] * p->n[2] > (1LL << 40)) return fail(CSLBM_EINVAL, "lattice too large");
+    return CSLBM_OK;
+}
+
+Layout layout(const cslbm_params* p)
+{
+    Layout L{};
+    L.N = (long long)p->n[0] * p->n[1] * p->n[2];
+    L.s_bytes = p->storage == CSLBM_FP32 ? 4 : (p->storage == CSLBM_FP64 ? 8 : 2);
+    L.r_bytes = p->storage == CSLBM_FP64 ? 8 : 4;
+    L.chunk = L.N < kMaxChunk ? L.N : kMaxChunk;
+    size_t o = 0;
+    for (int k = 0; k < 2; k++) { L.off_P[k] = o; o += al(19 * L.N * L.s_bytes); }
+    for (int k = 0; k < 2; k++) { L.off_H[k] = o; o += al(10 * L.N * L.r_bytes); }
+    for (int k = 0; k < 2; k++) { L.off_G[k] = o; o += al(25 * L.N * L.r_bytes); }
+    L.off_J = o; o += al(9 * L.N * sizeof(double));
+    L.off_jf = o; o += al(3 * L.N * L.r_bytes);
+    for (int k = 0; k < 6; k++) {
+        int a = k / 2;
+        bool periodic = (k & 1 ? p->bc_hi[a] : p->bc_lo[a]) == CSLBM_PERIODIC;
+        L.face_n[k] = (long long)p->n[(a + 1) % 3] * p->n[(a + 2) % 3];
+        L.off_face[k] = o;
+        if (!periodic) o += al(3 * L.face_n[k] * sizeof(double));
+    }
+    L.off_scratch = o; o += al(64 * sizeof(double));
+    L.off_staging = o; o += al(kStagingDoubles * L.chunk * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+__global__ void k_fill(double* p, long long n, double v)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+__global__ void k_fillf(float* p, long long n, float v)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+cslbm_status fill(cslbm_ctx* c, void* p, long long n, double v, bool fp64)
+{
+    unsigned nb = (unsigned)((n + 255) / 256);
+    if (fp64) k_fill<<<nb, 256, 0, c->stream>>>((double*)p, n, v);
+    else k_fillf<<<nb, 256, 0, c->stream>>>((float*)p, n, (float)v);
+    LAUNCH_CHECK("fill");
+    return CSLBM_OK;
+}
+
+// flat geometry into G[k]: sqrt g = 1, g^ij = delta, Gamma = 0
+cslbm_status set_flat(cslbm_ctx* c, int k)
+{
+    const bool d = c->r_bytes == 8;
+    char* g = (char*)c->G[k];
+    CUDA_TRY(cudaMemsetAsync(g, 0, 25 * c->N * c->r_bytes, c->stream));
+    const int ones[4] = {0, 1, 4, 6};  // sqrt g, g^00, g^11, g^22
+    for (int i : ones) {
+        cslbm_status s = fill(c, g + (size_t)i * c->N * c->r_bytes, c->N, 1.0, d);
+        if (s) return s;
+    }
+    return CSLBM_OK;
+}
+
+// copy `ncomp` components of `cnt` nodes starting at v0 from a [ncomp][N]
+// host or device array into the staging area as [ncomp][cnt].
+cslbm_status stage_in(cslbm_ctx* c, const double* src, int ncomp, long long v0, long long cnt, double* dst)
+{
+    for (int k = 0; k < ncomp; k++)
+        CUDA_TRY(cudaMemcpyAsync(dst + k * cnt, src + k * c->N + v0, cnt * sizeof(double), cudaMemcpyDefault,
+                                 c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status read_scratch(cslbm_ctx* c, double* out, int k)
+{
+    CUDA_TRY(cudaMemcpyAsync(out, c->scratch, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status metric_flag(cslbm_ctx* c)
+{
+    int hbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hbad, c->scratch + 32, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->metric_check_pending = 0;
+    if (hbad) return fail(CSLBM_EINVAL, "metric not positive definite (det g <= 0) at some node");
+    return CSLBM_OK;
+}
+
+// Metric kernel over all nodes into G[dst].  The det g > 0 flag is read back
+// at once (sync) or left pending for the next cslbm_check.
+cslbm_status run_metric(cslbm_ctx* c, const double* g6, const double* dg18, int on_device, int dst, bool sync)
+{
+    int* bad = (int*)(c->scratch + 32);
+    if (!c->metric_check_pending) CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    if (on_device) {
+        c->ops->metric(c, g6, dg18, c->N, 0, c->N, dst, bad);
+        c->launches++;
+        LAUNCH_CHECK("metric kernel");
+    } else {
+        for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
+            long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
+            cslbm_status s = stage_in(c, g6, 6, v0, cnt, c->staging);
+            if (!s) s = stage_in(c, dg18, 18, v0, cnt, c->staging + 6 * cnt);
+            if (s) return s;
+            c->ops->metric(c, c->staging, c->staging + 6 * cnt, cnt, v0, cnt, dst, bad);
+            c->launches++;
+            LAUNCH_CHECK("metric kernel");
+        }
+    }
+    if (sync) return metric_flag(c);
+    c->metric_check_pending = 1;
+    return CSLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cslbm_status cslbm_workspace_bytes(const cslbm_params* p, size_t* bytes)
+{
+    if (cslbm_status s = validate(p)) return s;
+    if (!bytes) return fail(CSLBM_EINVAL, "bytes is null");
+    *bytes = layout(p).total;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* stream, cslbm_ctx** out)
+{
+    if (cslbm_status s = validate(p)) return s;
+    if (!ws || !out) return fail(CSLBM_EINVAL, "workspace or out is null");
+    if ((uintptr_t)ws & 255) return fail(CSLBM_EINVAL, "workspace must be 256-byte aligned");
+    Layout L = layout(p);
+    if (bytes < L.total) return fail(CSLBM_ENOMEM, "workspace smaller than cslbm_workspace_bytes");
+    cslbm_ctx* c = new cslbm_ctx();
+    c->p = *p;
+    for (int a = 0; a < 3; a++) c->n[a] = p->n[a];
+    c->N = L.N;
+    c->theta = p->theta > 0 ? p->theta : 1.0 / 3.0;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->s_bytes = L.s_bytes;
+    c->r_bytes = L.r_bytes;
+    char* b = (char*)ws;
+    for (int k = 0; k < 2; k++) {
+        c->P[k] = b + L.off_P[k];
+        c->H[k] = b + L.off_H[k];
+        c->G[k] = b + L.off_G[k];
+    }
+    c->J = (double*)(b + L.off_J);
+    c->jf = b + L.off_jf;
+    for (int k = 0; k < 6; k++) {
+        int a = k / 2;
+        bool periodic = (k & 1 ? p->bc_hi[a] : p->bc_lo[a]) == CSLBM_PERIODIC;
+        c->face[k] = periodic ? nullptr : (double*)(b + L.off_face[k]);
+        c->face_n[k] = L.face_n[k];
+    }
+    c->scratch = (double*)(b + L.off_scratch);
+    c->staging = (double*)(b + L.off_staging);
+    c->chunk = L.chunk;
+    c->pc = c->hc = c->gc = 0;
+    c->has_state = 0;
+    c->ops = ops_for(p->storage);
+    cslbm_status s = CSLBM_OK;
+    if (cudaMemsetAsync(ws, 0, L.total, c->stream) != cudaSuccess) s = fail(CSLBM_ECUDA, "workspace memset failed");
+    if (!s) s = set_flat(c, 0);
+    if (!s) s = set_flat(c, 1);
+    if (!s) {
+        for (int i : {0, 4, 8}) {
+            s = fill(c, c->J + (size_t)i * c->N, c->N, 1.0, true);
+            if (s) break;
+        }
+    }
+    if (s) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_destroy(cslbm_ctx* c)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_set_metric(cslbm_ctx* c, const double* g6, const double* dg18, int on_device)
+{
+    if (!c || !g6 || !dg18) return fail(CSLBM_EINVAL, "null argument");
+    return run_metric(c, g6, dg18, on_device, c->gc, true);
+}
+
+cslbm_status cslbm_set_jacobian(cslbm_ctx* c, const double* J9, int on_device)
+{
+    if (!c || !J9) return fail(CSLBM_EINVAL, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(c->J, J9, 9 * c->N * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_update_metric(cslbm_ctx* c, const double* g6, const double* dg18, const double* Jnew9,
+                                 int on_device)
+{
+    if (!c || !g6 || !dg18 || !Jnew9) return fail(CSLBM_EINVAL, "null argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "update_metric before init_equilibrium");
+    if (cslbm_status s = run_metric(c, g6, dg18, on_device, 1 - c->gc, false)) return s;
+    if (on_device) {
+        c->ops->transform(c, Jnew9, c->N, 0, c->N);
+        c->launches++;
+        LAUNCH_CHECK("transform kernel");
+    } else {
+        for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
+            long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
+            if (cslbm_status s = stage_in(c, Jnew9, 9, v0, cnt, c->staging)) return s;
+            c->ops->transform(c, c->staging, cnt, v0, cnt);
+            c->launches++;
+            LAUNCH_CHECK("transform kernel");
+        }
+    }
+    c->pc ^= 1;
+    c->hc ^= 1;
+    c->gc ^= 1;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_init_equilibrium(cslbm_ctx* c, const double* rho, const double* u3, int on_device)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    for (int k = 0; k < 2; k++) {
+        CUDA_TRY(cudaMemsetAsync(c->P[k], 0, 19 * c->N * c->s_bytes, c->stream));
+        CUDA_TRY(cudaMemsetAsync(c->H[k], 0, 10 * c->N * c->r_bytes, c->stream));
+    }
+    if (on_device || (!rho && !u3)) {
+        c->ops->init_scatter(c, rho, u3, c->N, 0, c->N);
+        LAUNCH_CHECK("init kernel");
+    } else {
+        for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
+            long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
+            double* r = rho ? c->staging : nullptr;
+            double* u = u3 ? c->staging + cnt : nullptr;
+            if (rho)
+                if (cslbm_status s = stage_in(c, rho, 1, v0, cnt, r)) return s;
+            if (u3)
+                if (cslbm_status s = stage_in(c, u3, 3, v0, cnt, u)) return s;
+            c->ops->init_scatter(c, r, u, cnt, v0, cnt);
+            LAUNCH_CHECK("init kernel");
+        }
+    }
+    // forcing of the initial state, F(x, -dt) := F(x, 0)
+    c->ops->momentum_field(c);
+    LAUNCH_CHECK("momentum kernel");
+    c->ops->step(c, 1);
+    LAUNCH_CHECK("forcing kernel");
+    c->hc ^= 1;
+    c->ops->half_shift(c);
+    c->launches += 3;
+    LAUNCH_CHECK("shift kernel");
+    c->has_state = 1;
+    if (!on_device && (rho || u3)) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_set_boundary_velocity(cslbm_ctx* c, int axis, int side, const double* u3, int on_device)
+{
+    if (!c || axis < 0 || axis > 2 || side < 0 || side > 1) return fail(CSLBM_EINVAL, "bad face");
+    int k = axis * 2 + side;
+    int bc = side ? c->p.bc_hi[axis] : c->p.bc_lo[axis];
+    if (bc != CSLBM_WALL && bc != CSLBM_INFLOW) return fail(CSLBM_EINVAL, "face is not a wall or inflow face");
+    size_t bytes = 3 * c->face_n[k] * sizeof(double);
+    if (!u3) CUDA_TRY(cudaMemsetAsync(c->face[k], 0, bytes, c->stream));
+    else CUDA_TRY(cudaMemcpyAsync(c->face[k], u3, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream));
+    if (u3 && !on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_step(cslbm_ctx* c, int nsteps)
+{
+    if (!c || nsteps < 0) return fail(CSLBM_EINVAL, "bad argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "step before init_equilibrium");
+    for (int t = 0; t < nsteps; t++) {
+        if (c->prof) {
+            cudaEvent_t e[2];
+            CUDA_TRY(cudaEventCreate(&e[0]));
+            CUDA_TRY(cudaEventCreate(&e[1]));
+            c->ev.push_back(e[0]);
+            c->ev.push_back(e[1]);
+            CUDA_TRY(cudaEventRecord(e[0], c->stream));
+        }
+        c->ops->step(c, 0);
+        c->launches += 1;
+        LAUNCH_CHECK("step kernel");
+        if (c->prof) {
+            CUDA_TRY(cudaEventRecord(c->ev.back(), c->stream));
+            c->prof_steps++;
+        }
+        c->pc ^= 1;
+        c->hc ^= 1;
+    }
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_get_moments(cslbm_ctx* c, double* rho, double* u3, int cartesian, int on_device)
+{
+    if (!c || (!rho && !u3)) return fail(CSLBM_EINVAL, "null argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
+    if (on_device) {
+        c->ops->readout(c, rho, u3, c->N, 0, c->N, cartesian);
+        c->launches++;
+        LAUNCH_CHECK("readout kernel");
+        return CSLBM_OK;
+    }
+    for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
+        long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
+        double* r = c->staging;
+        double* u = c->staging + cnt;
+        c->ops->readout(c, rho ? r : nullptr, u3 ? u : nullptr, cnt, v0, cnt, cartesian);
+        c->launches++;
+        LAUNCH_CHECK("readout kernel");
+        if (rho) CUDA_TRY(cudaMemcpyAsync(rho + v0, r, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (u3)
+            for (int a = 0; a < 3; a++)
+                CUDA_TRY(cudaMemcpyAsync(u3 + a * c->N + v0, u + a * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_total_mass(cslbm_ctx* c, double* out)
+{
+    if (!c || !out) return fail(CSLBM_EINVAL, "null argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
+    CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 8 * sizeof(double), c->stream));
+    c->ops->mass(c, c->scratch);
+    c->launches++;
+    LAUNCH_CHECK("mass kernel");
+    return read_scratch(c, out, 1);
+}
+
+cslbm_status cslbm_wall_force(cslbm_ctx* c, int axis, int side, double out3[3])
+{
+    if (!c || !out3 || axis < 0 || axis > 2 || side < 0 || side > 1) return fail(CSLBM_EINVAL, "bad argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
+    CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 8 * sizeof(double), c->stream));
+    c->ops->wall_force(c, axis, side, c->scratch);
+    c->launches++;
+    LAUNCH_CHECK("wall-force kernel");
+    return read_scratch(c, out3, 3);
+}
+
+cslbm_status cslbm_check(cslbm_ctx* c)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
+    if (c->metric_check_pending)
+        if (cslbm_status s = metric_flag(c)) return s;
+    CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 8 * sizeof(double), c->stream));
+    c->ops->check(c, c->scratch);
+    c->launches++;
+    LAUNCH_CHECK("check kernel");
+    double bad = 0.0;
+    if (cslbm_status s = read_scratch(c, &bad, 1)) return s;
+    if (bad > 0.0) {
+        char m[96];
+        snprintf(m, sizeof m, "%.0f nodes with non-finite density or |v| > 0.3", bad);
+        return fail(CSLBM_EUNSTABLE, m);
+    }
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_state_bytes(const cslbm_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(CSLBM_EINVAL, "null argument");
+    *bytes = 19 * c->N * c->s_bytes + 10 * c->N * c->r_bytes;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_save_state(cslbm_ctx* c, void* buf, size_t bytes, int on_device)
+{
+    size_t need = 0;
+    if (cslbm_status s = cslbm_state_bytes(c, &need)) return s;
+    if (!buf || bytes < need) return fail(CSLBM_EINVAL, "buffer too small");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
+    size_t pb = 19 * c->N * c->s_bytes;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CUDA_TRY(cudaMemcpyAsync(buf, c->P[c->pc], pb, k, c->stream));
+    CUDA_TRY(cudaMemcpyAsync((char*)buf + pb, c->H[c->hc], need - pb, k, c->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_load_state(cslbm_ctx* c, const void* buf, size_t bytes, int on_device)
+{
+    size_t need = 0;
+    if (cslbm_status s = cslbm_state_bytes(c, &need)) return s;
+    if (!buf || bytes < need) return fail(CSLBM_EINVAL, "buffer too small");
+    size_t pb = 19 * c->N * c->s_bytes;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(cudaMemcpyAsync(c->P[c->pc], buf, pb, k, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->H[c->hc], (const char*)buf + pb, need - pb, k, c->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->has_state = 1;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_profile_enable(cslbm_ctx* c, int enable)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->prof = enable ? 1 : 0;
+    c->prof_steps = 0;
+    c->launches = 0;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_profile_read(cslbm_ctx* c, double* step_ms, long long* nsteps, long long* launches)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < c->ev.size(); k += 2) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        total += ms;
+    }
+    if (step_ms) *step_ms = total;
+    if (nsteps) *nsteps = c->prof_steps;
+    if (launches) *launches = c->launches;
+    return CSLBM_OK;
+}
+
+const char* cslbm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Internal context of the library (host side), shared by the C ABI and the
+// per-storage-format kernel units.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <vector>
+
+#include "../../include/cslbm.h"
+
+struct cslbm_ops;
+
+struct cslbm_ctx {
+    cslbm_params p;
+    int n[3];
+    long long N;
+    double theta;
+    cudaStream_t stream;
+    int device;
+    size_t s_bytes;  // bytes of one stored population
+    size_t r_bytes;  // bytes of one compute-precision value
+    void* P[2];      // [19][N] stored populations (pull layout, weight shifted)
+    void* H[2];      // [10][N] forcing-history coefficients
+    void* G[2];      // [25][N] geometry: sqrt(g), g^ij, Gamma
+    double* J;       // [9][N] current chart Jacobian (FP64)
+    void* jf;        // [3][N] momentum field (initial forcing only)
+    double* face[6]; // [3][face nodes] boundary velocity of non-periodic faces
+    long long face_n[6];
+    double* scratch; // 64 doubles of reduction space
+    double* staging; // host-transfer staging, chunk * 24 doubles
+    long long chunk; // nodes per staging chunk
+    int pc, hc, gc;  // current buffer of P, H, G
+    int has_state;
+    int metric_check_pending;  // a metric kernel ran without a host check
+    const cslbm_ops* ops;
+    // profiling
+    int prof;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs of profiled steps
+    long long prof_steps;
+    long long launches;
+};
+
+// Per-storage-format entry points (one kernel unit per format).
+// Node ranges: a launch touches nodes [v0, v0 + cnt); FP64 inputs given as
+// [components][stride] with the node's entry at (v - v0).
+struct cslbm_ops {
+    // geometry of G[dst] from g6/dg18; *bad set non-zero on det g <= 0
+    void (*metric)(const cslbm_ctx*, const double* g6, const double* dg18, long long stride,
+                   long long v0, long long cnt, int dst, int* bad);
+    // P[pc] slots of f^eq(rho,u) (history still zero)
+    void (*init_scatter)(const cslbm_ctx*, const double* rho, const double* u3, long long stride,
+                         long long v0, long long cnt);
+    // jf <- rho u of the current state
+    void (*momentum_field)(const cslbm_ctx*);
+    // one fused step P[pc],H[hc] -> P[1-pc],H[1-hc]; force_only: only H[1-hc]
+    // from the momentum field jf (initialisation)
+    void (*step)(const cslbm_ctx*, int force_only);
+    // P[pc] slots -= F/2 of H[hc] (end of initialisation)
+    void (*half_shift)(const cslbm_ctx*);
+    // chart change for nodes [v0, v0+cnt): P[pc],H[hc],G[gc] -> P[1-pc],H[1-hc] with G[1-gc]
+    void (*transform)(const cslbm_ctx*, const double* Jnew, long long stride, long long v0,
+                      long long cnt);
+    // rho, u (or v) of nodes [v0, v0+cnt) into out arrays with the given stride
+    void (*readout)(const cslbm_ctx*, double* rho, double* u3, long long stride, long long v0,
+                    long long cnt, int cartesian);
+    // scratch[0] += sum sqrt(g) rho
+    void (*mass)(const cslbm_ctx*, double* acc);
+    // acc[0..2] += wall force of face (axis, side)
+    void (*wall_force)(const cslbm_ctx*, int axis, int side, double* acc);
+    // acc[0] += number of unstable nodes
+    void (*check)(const cslbm_ctx*, double* acc);
+};
+
+extern const cslbm_ops cslbm_ops_fp32;
+extern const cslbm_ops cslbm_ops_fp16;
+extern const cslbm_ops cslbm_ops_bf16;
+extern const cslbm_ops cslbm_ops_fp64;

@@ -1,0 +1,625 @@
+// Kernels of the curved-space D3Q19 step, templated on the storage type S
+// of the populations and the compute type R.  Included once per storage
+// format by the inst_*.cu units, which instantiate the ops table.
+#pragma once
+
+#include "ctx.h"
+#include "lbm_device.cuh"
+
+namespace cslbm {
+
+constexpr int TPB = 256;
+
+inline Lat make_lat(const cslbm_ctx* c)
+{
+    Lat L;
+    for (int a = 0; a < 3; a++) {
+        L.n[a] = c->n[a];
+        L.bclo[a] = c->p.bc_lo[a];
+        L.bchi[a] = c->p.bc_hi[a];
+        L.fext[a] = c->p.fext[a];
+    }
+    L.N = c->N;
+    L.omega = 1.0 / c->p.tau;
+    L.kvisc = 1.0 - 0.5 / c->p.tau;
+    L.theta = c->theta;
+    for (int k = 0; k < 6; k++) L.face[k] = c->face[k];
+    return L;
+}
+
+inline unsigned nblocks(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+__device__ __forceinline__ void node_coords(const Lat& L, long long v, int& x, int& y, int& z)
+{
+    x = (int)(v % L.n[0]);
+    long long r = v / L.n[0];
+    y = (int)(r % L.n[1]);
+    z = (int)(r / L.n[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Metric update (App. A): inverse metric by cofactors in FP64, sqrt(det g),
+// then Gamma^i_jk = 1/2 g^il (d_j g_kl + d_k g_jl - d_l g_jk) in R.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, const double* __restrict__ dg18,
+                                                long long stride, long long v0, long long cnt, R* __restrict__ geo,
+                                                long long N, int* bad)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long v = v0 + t;
+    const double a = g6[0 * stride + t], b = g6[1 * stride + t], c = g6[2 * stride + t];
+    const double d = g6[3 * stride + t], e = g6[4 * stride + t], f = g6[5 * stride + t];
+    // g = [[a b c] [b d e] [c e f]]
+    const double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
+    const double det = a * A + b * B + c * C;
+    if (!(det > 0.0)) {
+        atomicOr(bad, 1);
+        return;
+    }
+    const double id = 1.0 / det;
+    double gi[6] = {A * id, B * id, C * id, (a * f - c * c) * id, (b * c - a * e) * id, (a * d - b * b) * id};
+    geo[v] = R(sqrt(det));
+#pragma unroll
+    for (int k = 0; k < 6; k++) geo[(1 + k) * N + v] = R(gi[k]);
+    R dg[3][6], gr[6];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int m = 0; m < 6; m++) dg[k][m] = R(dg18[(k * 6 + m) * stride + t]);
+#pragma unroll
+    for (int m = 0; m < 6; m++) gr[m] = R(gi[m]);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int k = j; k < 3; k++) {
+                R s = R(0);
+#pragma unroll
+                for (int l = 0; l < 3; l++) s += gr[s6(i, l)] * (dg[j][s6(k, l)] + dg[k][s6(j, l)] - dg[l][s6(j, k)]);
+                geo[(7 + i * 6 + s6(j, k)) * N + v] = R(0.5) * s;
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: the slots of P that node x's populations will be read from
+// get f^eq_l(x) - w_l (history still zero, so h = f).
+// ---------------------------------------------------------------------------
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_init_scatter(Lat L, const double* __restrict__ rho0, const double* __restrict__ u0,
+                                                      long long stride, long long v0, long long cnt,
+                                                      const R* __restrict__ geo, S* __restrict__ P)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long v = v0 + t;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    Geo<R> G;
+    load_metric(geo, L.N, v, G);
+    R rho = rho0 ? R(rho0[t]) : R(1);
+    R j[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) j[a] = u0 ? rho * R(u0[a * stride + t]) : R(0);
+    R a2[6];
+    feq_coeffs(rho, j, G.gi, R(L.theta), a2);
+    const R tr = a2[0] + a2[3] + a2[5];
+    const R b0 = rho - G.sg;  // f^eq - w = w/sqrt(g) [(rho - sqrt g) + ...]
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (r[a] < 0 || r[a] >= L.n[a]) {
+                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
+                else ok = false;
+            }
+        }
+        if (ok) Store<S>::st(P + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), hermite_l(l, G.isg, b0, j, a2, tr));
+    }
+}
+
+// P slots -= F_l(x)/2: the stored h = f - F(t - dt)/2 once the history exists.
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_half_shift(Lat L, S* __restrict__ P, const R* __restrict__ hist,
+                                                    const R* __restrict__ geo)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    Hist<R> H;
+    load_hist(hist, L.N, v, H);
+    const R isg = R(1) / geo[v];
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (r[a] < 0 || r[a] >= L.n[a]) {
+                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
+                else ok = false;
+            }
+        }
+        if (ok) {
+            S* p = P + (long long)l * L.N + nidx(L, r[0], r[1], r[2]);
+            Store<S>::st(p, Store<S>::ld(p) - R(0.5) * forcing_l(l, isg, H));
+        }
+    }
+}
+
+// macroscopic fields of a node from its (boundary-filled) populations
+template <class S, class R> struct NodeMoments {
+    R s[Q];
+    R m0, m1[3], m2[6];
+    R rho, j[3];
+    Hist<R> Hp;
+};
+
+template <class S, class R>
+__device__ __forceinline__ void node_moments(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                             const R* __restrict__ geo, int x, int y, int z, long long v, R sg,
+                                             NodeMoments<S, R>& M)
+{
+    node_pops<S, R>(L, P, hist, geo, x, y, z, M.s);
+    load_hist(hist, L.N, v, M.Hp);
+    sums(M.s, M.m0, M.m1, M.m2);
+    M.rho = sg * (R(1) + M.m0) + R(0.5) * M.Hp.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) M.j[a] = sg * M.m1[a] + R(0.5) * M.Hp.B[a];
+}
+
+// momentum field rho u^i of the current state (Eq. fields2)
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_momentum(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                  const R* __restrict__ geo, R* __restrict__ jf)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, P, hist, geo, x, y, z, v, geo[v], M);
+#pragma unroll
+    for (int a = 0; a < 3; a++) jf[a * L.N + v] = M.j[a];
+}
+
+// ---------------------------------------------------------------------------
+// Pieces of the step shared by the fused step kernel and the initial forcing.
+// ---------------------------------------------------------------------------
+// T = Pi^eq + (1 - 1/2tau)(Pi - Pi^eq), Pi^eq = rho theta g^-1 + j j / rho,
+// Pi = sqrt(g)(c_s^2 delta + m2) + C'/2    (Eq. fields3, App. B)
+template <class R>
+__device__ __forceinline__ void stress(const Lat& L, const Geo<R>& G, R rho, const R j[3], const R m2[6],
+                                       const Hist<R>& Hp, R T[6])
+{
+    const R ir = R(1) / rho, theta = R(L.theta), kv = R(L.kvisc);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a; b < 3; b++) {
+            const int k = s6(a, b);
+            R pieq = rho * theta * G.gi[k] + j[a] * j[b] * ir;
+            R pi = G.sg * ((a == b ? R(1.0 / 3.0) : R(0)) + m2[k]) + R(0.5) * Hp.C[k];
+            T[k] = pieq + kv * (pi - pieq);
+        }
+}
+
+// Collision (Eq. collision) written for the stored form s = h - w, with
+// h = f - F'/2:  f* = (1 - w) h + w f^eq + F - w/2 F'  (w = 1/tau), i.e.
+//   s* = (1 - w) s + w_l (w m0 + A/sqrt g) + Hermite_l(0, E1, E2),
+//   E1 = w j + B - w/2 B',  E2 = w a2^eq + b2 - w/2 b2'.
+template <class R>
+__device__ __forceinline__ void collide_coeffs(const Lat& L, const Geo<R>& G, R m0, R rho, const R j[3],
+                                               const Hist<R>& Hp, const Hist<R>& H, R& d0, R E1[3], R E2[6], R& trE2)
+{
+    const R om = R(L.omega);
+    R a2[6];
+    feq_coeffs(rho, j, G.gi, R(L.theta), a2);
+#pragma unroll
+    for (int a = 0; a < 3; a++) E1[a] = om * j[a] + H.B[a] - R(0.5) * om * Hp.B[a];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const bool dia = (k == 0 || k == 3 || k == 5);
+        R b2 = H.C[k] - (dia ? H.A * R(1.0 / 3.0) : R(0));
+        R b2p = Hp.C[k] - (dia ? Hp.A * R(1.0 / 3.0) : R(0));
+        E2[k] = om * a2[k] + b2 - R(0.5) * om * b2p;
+    }
+    trE2 = E2[0] + E2[3] + E2[5];
+    d0 = om * m0 + H.A * G.isg;
+}
+
+template <class R>
+__device__ __forceinline__ void store_hist(R* __restrict__ h, long long N, long long v, const Hist<R>& H)
+{
+    h[v] = H.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) h[(1 + a) * N + v] = H.B[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) h[(4 + a) * N + v] = H.C[a];
+}
+
+// Forcing coefficients of the current state (used once, at initialisation,
+// to set F(x, -dt) := F(x, 0)); the gradient reads the momentum field jf.
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_forcing(Lat L, const S* __restrict__ P, const R* __restrict__ hin,
+                                                 R* __restrict__ hout, const R* __restrict__ geo,
+                                                 const R* __restrict__ jf)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    Geo<R> G;
+    load_geo(geo, L.N, v, G);
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, P, hin, geo, x, y, z, v, G.sg, M);
+    R T[6];
+    stress(L, G, M.rho, M.j, M.m2, M.Hp, T);
+    // lattice gradient D[k][i] = 1/c_s^2 sum_l w_l c_l^k j^i(x + c_l) (App. D)
+    R D[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int i = 0; i < 3; i++) D[k][i] = R(0);
+    for (int l = 1; l < Q; l++) {
+        const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        const R wl = R(3.0 * wq(l));
+        for (int i = 0; i < 3; i++) {
+            R jn = jsite<R>(L, jf, i, x + cx, y + cy, z + cz);
+            D[0][i] += (wl * cx) * jn;
+            D[1][i] += (wl * cy) * jn;
+            D[2][i] += (wl * cz) * jn;
+        }
+    }
+    Hist<R> H;
+    forcing_moments(L, G, M.j, T, D, H);
+    store_hist(hout, L.N, v, H);
+}
+
+// ---------------------------------------------------------------------------
+// Chart change (Sec. IV.B), node-wise: D phi = Jnew^-1 Jold; a_(0) kept,
+// a_(1) -> D a_(1), Pi -> D Pi D^T (or a_(2) -> D a_(2) D^T), recomposed with
+// the new sqrt(g); the history's A, B, C as scalar, vector, rank-2 tensor.
+// Writes the transformed state into the other buffers (same pull slots).
+// ---------------------------------------------------------------------------
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                   const R* __restrict__ hin, R* __restrict__ hout,
+                                                   const R* __restrict__ geo_old, const R* __restrict__ geo_new,
+                                                   double* __restrict__ J, const double* __restrict__ Jnew,
+                                                   long long stride, long long v0, long long cnt, int literal)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long v = v0 + t;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    const R sgo = geo_old[v];
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, Pin, hin, geo_old, x, y, z, v, sgo, M);
+    // D phi in FP64: Jnew^-1 Jold
+    double Jo[9], Jn[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        Jo[k] = J[k * L.N + v];
+        Jn[k] = Jnew[k * stride + t];
+    }
+    double inv[9];
+    {
+        const double c00 = Jn[4] * Jn[8] - Jn[5] * Jn[7], c01 = Jn[5] * Jn[6] - Jn[3] * Jn[8], c02 = Jn[3] * Jn[7] - Jn[4] * Jn[6];
+        const double det = Jn[0] * c00 + Jn[1] * c01 + Jn[2] * c02, id = 1.0 / det;
+        inv[0] = c00 * id;
+        inv[3] = c01 * id;
+        inv[6] = c02 * id;
+        inv[1] = (Jn[2] * Jn[7] - Jn[1] * Jn[8]) * id;
+        inv[4] = (Jn[0] * Jn[8] - Jn[2] * Jn[6]) * id;
+        inv[7] = (Jn[1] * Jn[6] - Jn[0] * Jn[7]) * id;
+        inv[2] = (Jn[1] * Jn[5] - Jn[2] * Jn[4]) * id;
+        inv[5] = (Jn[2] * Jn[3] - Jn[0] * Jn[5]) * id;
+        inv[8] = (Jn[0] * Jn[4] - Jn[1] * Jn[3]) * id;
+    }
+    R Dp[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < 3; m++) s += inv[i * 3 + m] * Jo[m * 3 + k];
+            Dp[i][k] = R(s);
+        }
+#pragma unroll
+    for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
+    // moments of f: a0 = rho, a1 = j, M2 = Pi (or a_(2))
+    R M2[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const bool dia = (k == 0 || k == 3 || k == 5);
+        M2[k] = sgo * ((dia ? R(1.0 / 3.0) : R(0)) + M.m2[k]) + R(0.5) * M.Hp.C[k];
+        if (literal && dia) M2[k] -= M.rho * R(1.0 / 3.0);
+    }
+    auto vec = [&](const R in[3], R out[3]) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) out[i] = Dp[i][0] * in[0] + Dp[i][1] * in[1] + Dp[i][2] * in[2];
+    };
+    auto ten = [&](const R in[6], R out[6]) {
+        R tmp[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int m = 0; m < 3; m++)
+                tmp[i][m] = Dp[i][0] * in[s6(0, m)] + Dp[i][1] * in[s6(1, m)] + Dp[i][2] * in[s6(2, m)];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = i; k < 3; k++) out[s6(i, k)] = tmp[i][0] * Dp[k][0] + tmp[i][1] * Dp[k][1] + tmp[i][2] * Dp[k][2];
+    };
+    R j2[3], P2[6];
+    vec(M.j, j2);
+    ten(M2, P2);
+    if (!literal) {
+        P2[0] -= M.rho * R(1.0 / 3.0);
+        P2[3] -= M.rho * R(1.0 / 3.0);
+        P2[5] -= M.rho * R(1.0 / 3.0);
+    }
+    // history: A scalar, B vector, C (or, with literal, b_(2) = C - c_s^2 delta A) rank 2
+    Hist<R> Hn;
+    Hn.A = M.Hp.A;
+    vec(M.Hp.B, Hn.B);
+    R Cs[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) Cs[k] = M.Hp.C[k] - ((literal && (k == 0 || k == 3 || k == 5)) ? M.Hp.A * R(1.0 / 3.0) : R(0));
+    ten(Cs, Hn.C);
+    if (literal) {
+        Hn.C[0] += Hn.A * R(1.0 / 3.0);
+        Hn.C[3] += Hn.A * R(1.0 / 3.0);
+        Hn.C[5] += Hn.A * R(1.0 / 3.0);
+    }
+    const R sgn = geo_new[v], isgn = R(1) / sgn;
+    const R trP2 = P2[0] + P2[3] + P2[5];
+    hout[v] = Hn.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) hout[(1 + a) * L.N + v] = Hn.B[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) hout[(4 + a) * L.N + v] = Hn.C[a];
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (r[a] < 0 || r[a] >= L.n[a]) {
+                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
+                else ok = false;
+            }
+        }
+        if (!ok) continue;
+        // f~ - F~/2 - w  with  f~ - w = w/sqrt(g~) [(rho - sqrt g~) + ...]
+        R val = hermite_l(l, isgn, M.rho - sgn, j2, P2, trP2) - R(0.5) * forcing_l(l, isgn, Hn);
+        Store<S>::st(Pout + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), val);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// readout and reductions
+// ---------------------------------------------------------------------------
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_readout(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                 const R* __restrict__ geo, const double* __restrict__ J,
+                                                 double* __restrict__ rho_out, double* __restrict__ u_out,
+                                                 long long stride, long long v0, long long cnt, int cartesian)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long v = v0 + t;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, P, hist, geo, x, y, z, v, geo[v], M);
+    double u[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) u[a] = double(M.j[a]) / double(M.rho);
+    if (rho_out) rho_out[t] = double(M.rho);
+    if (u_out) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double s = u[a];
+            if (cartesian) s = J[(a * 3 + 0) * L.N + v] * u[0] + J[(a * 3 + 1) * L.N + v] * u[1] + J[(a * 3 + 2) * L.N + v] * u[2];
+            u_out[a * stride + t] = s;
+        }
+    }
+}
+
+// FP64 block reduction of up to 3 values, one atomic per block and value.
+template <int K>
+__device__ __forceinline__ void block_reduce_add(double (&val)[K], double* acc)
+{
+    __shared__ double part[K][TPB / 32];
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_down_sync(0xffffffffu, val[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) part[k][wid] = val[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = lane < (TPB / 32) ? part[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) atomicAdd(acc + k, s);
+        }
+    }
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_mass(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                              const R* __restrict__ geo, double* acc)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double val[1] = {0.0};
+    if (v < L.N) {
+        int x, y, z;
+        node_coords(L, v, x, y, z);
+        const R sg = geo[v];
+        NodeMoments<S, R> M;
+        node_moments<S, R>(L, P, hist, geo, x, y, z, v, sg, M);
+        val[0] = double(sg) * double(M.rho);
+    }
+    block_reduce_add<1>(val, acc);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_wall_force(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                    const R* __restrict__ geo, const double* __restrict__ J,
+                                                    int axis, int side, double* acc)
+{
+    // one thread per node of the face
+    const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+    long long nf = (long long)L.n[a1] * L.n[a2];
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double val[3] = {0.0, 0.0, 0.0};
+    if (t < nf) {
+        int r[3];
+        r[axis] = side ? L.n[axis] - 1 : 0;
+        r[a1] = (int)(t % L.n[a1]);
+        r[a2] = (int)(t / L.n[a1]);
+        const long long v = nidx(L, r[0], r[1], r[2]);
+        Geo<R> G;
+        load_metric(geo, L.N, v, G);
+        NodeMoments<S, R> M;
+        node_moments<S, R>(L, P, hist, geo, r[0], r[1], r[2], v, G.sg, M);
+        const R ir = R(1) / M.rho, theta = R(L.theta), kv = R(L.kvisc);
+        R Tn[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int k = s6(i, axis);
+            R pieq = M.rho * theta * G.gi[k] + M.j[i] * M.j[axis] * ir;
+            R pi = G.sg * ((i == axis ? R(1.0 / 3.0) : R(0)) + M.m2[k]) + R(0.5) * M.Hp.C[k];
+            Tn[i] = pieq + kv * (pi - pieq);
+        }
+        const double sgn = side ? 1.0 : -1.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; i++) s += J[(a * 3 + i) * L.N + v] * double(Tn[i]);
+            val[a] = sgn * s * double(G.sg);
+        }
+    }
+    block_reduce_add<3>(val, acc);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_check(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                               const R* __restrict__ geo, const double* __restrict__ J, double* acc)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double val[1] = {0.0};
+    if (v < L.N) {
+        int x, y, z;
+        node_coords(L, v, x, y, z);
+        NodeMoments<S, R> M;
+        node_moments<S, R>(L, P, hist, geo, x, y, z, v, geo[v], M);
+        double u[3], s2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) u[a] = double(M.j[a]) / double(M.rho);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double va = J[(a * 3) * L.N + v] * u[0] + J[(a * 3 + 1) * L.N + v] * u[1] + J[(a * 3 + 2) * L.N + v] * u[2];
+            s2 += va * va;
+        }
+        const bool bad = !(double(M.rho) > 0.0) || !(s2 <= 0.09);  // false for NaN too
+        val[0] = bad ? 1.0 : 0.0;
+    }
+    block_reduce_add<1>(val, acc);
+}
+
+}  // namespace cslbm
+
+#include "fused_step.cuh"
+
+namespace cslbm {
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <class S, class R> struct Launch {
+    static S* P(const cslbm_ctx* c, int k) { return (S*)c->P[k]; }
+    static R* H(const cslbm_ctx* c, int k) { return (R*)c->H[k]; }
+    static R* G(const cslbm_ctx* c, int k) { return (R*)c->G[k]; }
+
+    static void metric(const cslbm_ctx* c, const double* g6, const double* dg18, long long stride, long long v0,
+                       long long cnt, int dst, int* bad)
+    {
+        k_metric<R><<<nblocks(cnt), TPB, 0, c->stream>>>(g6, dg18, stride, v0, cnt, G(c, dst), c->N, bad);
+    }
+    static void init_scatter(const cslbm_ctx* c, const double* rho, const double* u3, long long stride, long long v0,
+                             long long cnt)
+    {
+        k_init_scatter<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), rho, u3, stride, v0, cnt,
+                                                                  G(c, c->gc), P(c, c->pc));
+    }
+    static void momentum_field(const cslbm_ctx* c)
+    {
+        k_momentum<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                               (R*)c->jf);
+    }
+    static void step(const cslbm_ctx* c, int force_only)
+    {
+        Lat L = make_lat(c);
+        if (force_only) {
+            k_forcing<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(L, P(c, c->pc), H(c, c->hc), H(c, 1 - c->hc),
+                                                                 G(c, c->gc), (const R*)c->jf);
+            return;
+        }
+        launch_fused_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
+    }
+    static void half_shift(const cslbm_ctx* c)
+    {
+        k_half_shift<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc));
+    }
+    static void transform(const cslbm_ctx* c, const double* Jnew, long long stride, long long v0, long long cnt)
+    {
+        k_transform<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc),
+                                                               H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, Jnew,
+                                                               stride, v0, cnt, c->p.transform_flags & 1);
+    }
+    static void readout(const cslbm_ctx* c, double* rho, double* u3, long long stride, long long v0, long long cnt,
+                        int cartesian)
+    {
+        k_readout<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), c->J,
+                                                             rho, u3, stride, v0, cnt, cartesian);
+    }
+    static void mass(const cslbm_ctx* c, double* acc)
+    {
+        k_mass<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), acc);
+    }
+    static void wall_force(const cslbm_ctx* c, int axis, int side, double* acc)
+    {
+        const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+        long long nf = (long long)c->n[a1] * c->n[a2];
+        k_wall_force<S, R><<<nblocks(nf), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                               c->J, axis, side, acc);
+    }
+    static void check(const cslbm_ctx* c, double* acc)
+    {
+        k_check<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), c->J,
+                                                            acc);
+    }
+    static constexpr cslbm_ops ops()
+    {
+        return cslbm_ops{&metric, &init_scatter, &momentum_field, &step, &half_shift,
+                         &transform, &readout, &mass, &wall_force, &check};
+    }
+};
+
+}  // namespace cslbm

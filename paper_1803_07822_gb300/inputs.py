@@ -246,13 +246,13 @@ def plain_fp64_channel(n=(16, 16, 32)):
 
 
 def dynamic_channel(n=(128, 128, 256), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
-                    t=0.0, period=2000.0):
+                    t=0.0, period=2000.0, kmax=4, lmax=3):
     """Walls across axis 0, periodic span, parabolic inflow at z = 0 and
     outflow at z = n2-1; deformation scaled by a(t) = sin^2(pi t/period)."""
     nu = (tau - 0.5) / 3.0
     H = n[0] - 1
     umax = re * nu / H
-    base = fourier_deformation(n, n_modes, amp, seed, flow_periodic=False)
+    base = fourier_deformation(n, n_modes, amp, seed, flow_periodic=False, kmax=kmax, lmax=lmax)
     a, adot = time_law(t, period)
     dfm = base.scaled(a)
     chart = channel_chart(n, dfm)

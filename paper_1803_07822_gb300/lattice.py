@@ -1,0 +1,185 @@
+"""Python front end of the C ABI: one curved-space D3Q19 channel per object.
+
+PyTorch supplies the device memory (the workspace is a uint8 tensor) and the
+stream; every step of the method runs in the library's CUDA kernels.  Inputs
+may be CUDA tensors (passed as device pointers) or numpy arrays (host
+pointers; the library stages the copies).  There is no CPU path: without a
+CUDA device the constructor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import call
+
+STORAGE = {"fp32": _abi.FP32, "fp16": _abi.FP16S, "bf16": _abi.BF16S, "fp64": _abi.FP64}
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("cslbm needs a CUDA device (GB300); no CPU fallback exists")
+    return torch
+
+
+class CurvedLattice:
+    """A D3Q19 lattice of shape n = (n0, n1, n2) carrying a metric field.
+
+    bc_lo / bc_hi: per-axis face rules (PERIODIC, WALL, INFLOW, OUTFLOW);
+    tau: BGK relaxation time; fext: contravariant body-force density;
+    storage: "fp32", "fp16", "bf16" (weight-shifted, FP32 arithmetic) or
+    "fp64"; literal_a2: transform a_(2) itself on chart changes.
+    """
+
+    def __init__(self, n, bc_lo=(0, 0, 0), bc_hi=None, tau=0.8, theta=0.0, fext=(0.0, 0.0, 0.0),
+                 storage="fp32", literal_a2=False, device=None, stream=None):
+        torch = _torch()
+        _abi.load()
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        bc_hi = bc_lo if bc_hi is None else bc_hi
+        self.params = _abi.Params((ctypes.c_int * 3)(*self.n), (ctypes.c_int * 3)(*bc_lo),
+                                  (ctypes.c_int * 3)(*bc_hi), float(tau), float(theta),
+                                  (ctypes.c_double * 3)(*fext), STORAGE[storage], int(bool(literal_a2)))
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        nbytes = ctypes.c_size_t(0)
+        call("cslbm_workspace_bytes", ctypes.byref(self.params), ctypes.byref(nbytes))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self.ctx = ctypes.c_void_p()
+        call("cslbm_create", ctypes.byref(self.params), self.workspace.data_ptr(), nbytes.value,
+             self.stream.cuda_stream, ctypes.byref(self.ctx))
+
+    # -- marshalling --------------------------------------------------------
+    def _arg(self, a, rows):
+        """(pointer, on_device, keep-alive) for an FP64 [rows, N]-shaped input."""
+        if a is None:
+            return None, 1, None
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.device.type != "cuda":
+                a = a.detach().to(torch.float64).contiguous().numpy()
+            else:
+                t = a.detach().to(self.device, torch.float64).contiguous()
+                if t.numel() != rows:
+                    raise ValueError(f"expected {rows} values, got {t.numel()}")
+                return t.data_ptr(), 1, t
+        h = np.ascontiguousarray(a, dtype=np.float64)
+        if h.size != rows:
+            raise ValueError(f"expected {rows} values, got {h.size}")
+        return h.ctypes.data, 0, h
+
+    def face_nodes(self, axis):
+        return self.n[(axis + 1) % 3] * self.n[(axis + 2) % 3]
+
+    # -- geometry -----------------------------------------------------------
+    def set_metric(self, g6, dg18):
+        p1, d1, k1 = self._arg(g6, 6 * self.N)
+        p2, d2, k2 = self._arg(dg18, 18 * self.N)
+        if d1 != d2:
+            raise ValueError("g6 and dg18 must both be host or both device arrays")
+        call("cslbm_set_metric", self.ctx, p1, p2, d1)
+
+    def set_jacobian(self, J9):
+        p, d, k = self._arg(J9, 9 * self.N)
+        call("cslbm_set_jacobian", self.ctx, p, d)
+
+    def update_metric(self, g6, dg18, J9):
+        p1, d1, k1 = self._arg(g6, 6 * self.N)
+        p2, d2, k2 = self._arg(dg18, 18 * self.N)
+        p3, d3, k3 = self._arg(J9, 9 * self.N)
+        if not (d1 == d2 == d3):
+            raise ValueError("metric inputs must all be host or all device arrays")
+        call("cslbm_update_metric", self.ctx, p1, p2, p3, d1)
+
+    def set_chart(self, chart):
+        """Metric and Jacobian of an inputs.Chart (no transformation)."""
+        self.set_metric(chart.g6, chart.dg18)
+        self.set_jacobian(chart.J9)
+
+    # -- state --------------------------------------------------------------
+    def init_equilibrium(self, rho=None, u=None):
+        p1, d1, k1 = self._arg(rho, self.N)
+        p2, d2, k2 = self._arg(u, 3 * self.N)
+        on_dev = d1 if rho is not None else d2
+        call("cslbm_init_equilibrium", self.ctx, p1, p2, on_dev)
+
+    def set_boundary_velocity(self, axis, side, u3):
+        p, d, k = self._arg(u3, 3 * self.face_nodes(axis))
+        call("cslbm_set_boundary_velocity", self.ctx, axis, side, p, d)
+
+    def step(self, nsteps=1):
+        call("cslbm_step", self.ctx, int(nsteps))
+
+    def moments(self, cartesian=False, host=True):
+        """(rho [N], u [3, N]) FP64 -- numpy arrays (host=True) or CUDA tensors."""
+        if host:
+            rho = np.empty(self.N)
+            u = np.empty((3, self.N))
+            call("cslbm_get_moments", self.ctx, rho.ctypes.data, u.ctypes.data, int(cartesian), 0)
+            return rho, u
+        torch = _torch()
+        rho = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        u = torch.empty((3, self.N), dtype=torch.float64, device=self.device)
+        call("cslbm_get_moments", self.ctx, rho.data_ptr(), u.data_ptr(), int(cartesian), 1)
+        return rho, u
+
+    def total_mass(self):
+        out = ctypes.c_double(0.0)
+        call("cslbm_total_mass", self.ctx, ctypes.byref(out))
+        return out.value
+
+    def wall_force(self, axis, side):
+        out = (ctypes.c_double * 3)()
+        call("cslbm_wall_force", self.ctx, axis, side, out)
+        return np.array(out[:])
+
+    def check(self):
+        """True if the state is finite and subsonic; False on CSLBM_EUNSTABLE."""
+        lib = _abi.load()
+        st = lib.cslbm_check(self.ctx)
+        if st == _abi.EUNSTABLE:
+            return False
+        if st != _abi.OK:
+            raise _abi.CslbmError(st, "cslbm_check", lib.cslbm_last_error().decode())
+        return True
+
+    def state_bytes(self):
+        n = ctypes.c_size_t(0)
+        call("cslbm_state_bytes", self.ctx, ctypes.byref(n))
+        return n.value
+
+    def save_state(self):
+        torch = _torch()
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        call("cslbm_save_state", self.ctx, buf.data_ptr(), buf.numel(), 1)
+        return buf
+
+    def load_state(self, buf):
+        call("cslbm_load_state", self.ctx, buf.data_ptr(), buf.numel(), 1)
+
+    def profile(self, enable=True):
+        """Start (or stop) event timing of each LBM step and launch counting."""
+        call("cslbm_profile_enable", self.ctx, int(bool(enable)))
+
+    def profile_read(self):
+        """(total ms of the profiled steps, number of steps, kernel launches)."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_longlong(0)
+        k = ctypes.c_longlong(0)
+        call("cslbm_profile_read", self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k))
+        return ms.value, n.value, k.value
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            _abi.load().cslbm_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

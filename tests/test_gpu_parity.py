@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; element-by-element comparison of density
+and velocity (relative L2 over all nodes), mass and wall force.  Bars:
+FP64 storage 1e-11, FP32 storage 1e-5 (the method's FP32 target after 1000
+steps), FP16/BF16 weight-shifted storage a stated bound.  Sizes are odd and
+ragged on purpose (not multiples of the kernels' tiles).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_07822_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+W, P, IN, OUT = oracle.WALL, oracle.PERIODIC, oracle.INFLOW, oracle.OUTFLOW
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def make_pair(w, storage, literal=False):
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+    kw = dict(tau=w["tau"], fext=w["fext"])
+    g = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], storage=storage, literal_a2=literal, **kw)
+    o = oracle.Lattice(w["n"], w["bc_lo"], w["bc_hi"], literal_a2=literal, **kw)
+    ch = w["chart"]
+    g.set_chart(ch)
+    o.set_metric(ch.g6, ch.dg18)
+    for (axis, side), u in w.get("faces", {}).items():
+        g.set_boundary_velocity(axis, side, u)
+        o.set_face_velocity(axis, side, u)
+    return g, o
+
+
+def compare(g, o, J9, tol, tag=""):
+    rg, ug = g.moments(cartesian=True)
+    ro, uo = o.moments(J9)
+    er, eu = rel(rg, ro), rel(ug, uo)
+    assert np.isfinite(ug).all()
+    assert er < tol and eu < tol, f"{tag} rho {er:.3e} u {eu:.3e} (tol {tol})"
+    return er, eu
+
+
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_plain_channel_1000_steps(storage):
+    """16x16x32 periodic channel, static one-mode metric (5 %), walls, body
+    force, tau = 0.8, rho = 1, u = 0, 1000 steps."""
+    w = I.plain_fp64_channel()
+    g, o = make_pair(w, storage)
+    g.init_equilibrium()
+    o.init()
+    rg, ug = g.moments()
+    assert rel(rg, o.moments()[0]) < TOL[storage]  # rest at t = 0
+    assert np.abs(ug).max() < (1e-12 if storage == "fp64" else 1e-6)
+    g.step(1000)
+    o.step(1000)
+    compare(g, o, w["chart"].J9, TOL[storage], "t=1000")
+    mo, mg = o.mass(), g.total_mass()
+    assert abs(mg - mo) / mo < (1e-12 if storage == "fp64" else 1e-6)
+    for side in (0, 1):
+        fo = o.wall_force(0, side, w["chart"].J9)
+        fg = g.wall_force(0, side)
+        assert rel(fg, fo) < (1e-10 if storage == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_ragged_inflow_outflow_moving_wall(storage):
+    """Odd sizes, inflow/outflow along the flow axis, a moving top wall,
+    random initial density and velocity, a 4-mode tapered deformation."""
+    n = (13, 7, 29)
+    dfm = I.fourier_deformation(n, 4, 0.06, seed=77, flow_periodic=False, kmax=2, lmax=1)
+    ch = I.channel_chart(n, dfm)
+    rng = np.random.default_rng(5)
+    faces = {(2, 0): I.inflow_profile(n, ch, 0.04), (0, 1): 0.01 * rng.standard_normal((3, 7 * 29))}
+    w = dict(n=n, bc_lo=(W, P, IN), bc_hi=(W, P, OUT), tau=0.7, fext=(1e-5, 0.0, 2e-5), chart=ch, faces=faces)
+    g, o = make_pair(w, storage)
+    N = int(np.prod(n))
+    rho0 = 1 + 0.01 * rng.standard_normal(N)
+    u0 = 0.02 * rng.standard_normal((3, N))
+    g.init_equilibrium(rho0, u0)
+    o.init(rho0, u0)
+    g.step(150)
+    o.step(150)
+    compare(g, o, ch.J9, TOL[storage])
+
+
+def test_walls_on_every_axis_edges_and_corners():
+    """All six faces are walls (edges and corners take the wall rule with the
+    diagonal inner node); one wall moves."""
+    n = (6, 7, 9)
+    dfm = I.fourier_deformation(n, 2, 0.04, seed=3, flow_periodic=False, kmax=1, lmax=1)
+    ch = I.channel_chart(n, dfm)
+    rng = np.random.default_rng(6)
+    faces = {(2, 1): 0.02 * rng.standard_normal((3, 6 * 7))}
+    w = dict(n=n, bc_lo=(W, W, W), bc_hi=(W, W, W), tau=0.9, fext=(0.0, 1e-5, 0.0), chart=ch, faces=faces)
+    for storage in ("fp64", "fp32"):
+        g, o = make_pair(w, storage)
+        g.init_equilibrium()
+        o.init()
+        g.step(120)
+        o.step(120)
+        compare(g, o, ch.J9, TOL[storage], storage)
+        for axis in range(3):
+            for side in (0, 1):
+                assert rel(g.wall_force(axis, side), o.wall_force(axis, side, ch.J9)) < 100 * TOL[storage]
+
+
+@pytest.mark.parametrize("literal", [False, True])
+def test_dynamic_metric_with_transform(literal):
+    """Time-dependent deformation (dynamic channel generator at a small size):
+    the metric and the distributions are re-transformed every 10 steps."""
+    n = (17, 9, 33)
+    w = I.dynamic_channel(n=n, seed=2000, n_modes=6, amp=0.06, tau=0.6, re=20.0, period=400.0, kmax=2,
+                          lmax=1)
+    w["chart"], w["faces"] = I.dynamic_channel_at(w, 0.0)
+    for storage in ("fp64", "fp32"):
+        g, o = make_pair(w, storage, literal)
+        g.init_equilibrium()
+        o.init()
+        ch_old = w["chart"]
+        for t in range(10, 110, 10):
+            g.step(10)
+            o.step(10)
+            ch, faces = I.dynamic_channel_at(w, float(t))
+            g.update_metric(ch.g6, ch.dg18, ch.J9)
+            o.transform(ch.g6, ch.dg18, ch_old.J9, ch.J9)
+            for (axis, side), u in faces.items():
+                g.set_boundary_velocity(axis, side, u)
+                o.set_face_velocity(axis, side, u)
+            ch_old = ch
+        g.step(5)
+        o.step(5)
+        compare(g, o, ch_old.J9, TOL[storage], storage)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 3e-2), ("bf16", 1e-1)])
+def test_reduced_precision_storage_error(storage, tol):
+    """Weight-shifted FP16/BF16 storage with FP32 arithmetic, error vs the
+    FP64 oracle on the plain channel after 1000 steps (stated bounds)."""
+    w = I.plain_fp64_channel()
+    g, o = make_pair(w, storage)
+    g.init_equilibrium()
+    o.init()
+    g.step(1000)
+    o.step(1000)
+    rg, ug = g.moments(cartesian=True)
+    ro, uo = o.moments(w["chart"].J9)
+    assert rel(rg, ro) < 1e-3
+    assert rel(ug, uo) < tol
+
+
+def test_flat_periodic_random_state_fp64():
+    n = (5, 6, 7)
+    w = dict(n=n, bc_lo=(P, P, P), bc_hi=(P, P, P), tau=0.55, fext=(1e-5, 2e-5, -1e-5), chart=I.flat_chart(n))
+    g, o = make_pair(w, "fp64")
+    rng = np.random.default_rng(8)
+    N = int(np.prod(n))
+    rho0 = 1 + 0.03 * rng.standard_normal(N)
+    u0 = 0.05 * rng.standard_normal((3, N))
+    g.init_equilibrium(rho0, u0)
+    o.init(rho0, u0)
+    g.step(200)
+    o.step(200)
+    compare(g, o, w["chart"].J9, 1e-12)
+    assert abs(g.total_mass() - o.mass()) / o.mass() < 1e-13
+
+
+def test_host_and_device_inputs_agree_and_state_roundtrip():
+    import torch
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+    w = I.plain_fp64_channel()
+    ch = w["chart"]
+    a = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+    b = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+    a.set_chart(ch)
+    dev = lambda x: torch.as_tensor(x, device="cuda")
+    b.set_metric(dev(ch.g6), dev(ch.dg18))
+    b.set_jacobian(dev(ch.J9))
+    a.init_equilibrium()
+    b.init_equilibrium()
+    a.step(20)
+    b.step(20)
+    ra, ua = a.moments()
+    rb, ub = b.moments(host=False)
+    assert np.array_equal(ra, rb.cpu().numpy()) and np.array_equal(ua, ub.cpu().numpy())
+    snap = a.save_state()
+    a.step(7)
+    r1, u1 = a.moments()
+    a.load_state(snap)
+    a.step(7)
+    r2, u2 = a.moments()
+    assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
+    assert a.check()
