@@ -1,7 +1,8 @@
 """Throughput benchmark of the curved-space LBM hot path on GB300.
 
-Workload (default): the dynamic deformed channel -- 128 x 128 x 256 nodes,
-walls across axis 0, periodic span, parabolic inflow / outflow along the flow
+Workload (default): the dynamic deformed channel -- 128 x 128 x 256 nodes
+(128 span on axis 0, 256 along the flow on axis 1, 128 wall-normal on axis
+2), walls across axis 2, periodic span, parabolic inflow / outflow along the flow
 axis, tau = 0.6 (Re ~ 100), a 16-mode seeded wall deformation of 10 %
 amplitude under the time law sin^2(pi t / 2000), FP32 storage.  One bench
 step is one cycle of that schedule: metric update + transformation of f
@@ -46,11 +47,11 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
 
 def workload_spec(name):
     if name == "dynamic":
-        return dict(n=(128, 128, 256), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
+        return dict(n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
                     storage="fp32", label="deformed channel 128x128x256, dynamic metric (16 modes, 10 %), "
                                           "inflow/outflow, tau 0.6, Re 100, FP32, transform every 10 steps")
     if name == "crop64":
-        return dict(n=(64, 64, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0, storage="fp32",
+        return dict(n=(64, 128, 64), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0, storage="fp32",
                     label="deformed channel 64x64x128 (profiling case), dynamic metric, inflow/outflow, FP32")
     if name == "target256":
         return dict(n=(256, 256, 256), seed=3000, n_modes=8, amp=0.08, tau=0.6, re=100.0, storage="fp32",

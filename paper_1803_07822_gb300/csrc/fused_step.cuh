@@ -25,9 +25,22 @@ constexpr int FX = 32, FY = 8, FT = FX * FY;  // interior tile and threads per C
 constexpr int EX = FX + 2, EY = FY + 2;       // tile with its ring
 
 template <class R> struct FusedSmem {
-    R s[2][Q][FY][FX];  // populations (h - w) of the current and the next plane
-    R j[3][3][EY][EX];  // rho u of three consecutive planes [slot][component][y][x]
+    R s[2][Q][FY][FX];      // populations (h - w) of the current and the next plane
+    R j[3][3][EY][EX];      // rho u of three consecutive planes [slot][component][y][x]
+    R geo[NGEO][FY][FX];    // geometry of the plane being stepped (cp.async prefetch)
+    R hist[NHIST][FY][FX];  // its forcing history
 };
+
+// asynchronous global -> shared copies of one 4- or 8-byte value
+template <class R>
+__device__ __forceinline__ void cp_async(R* smem, const R* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (sizeof(R) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ int pslot(int z) { return ((z % 3) + 3) % 3; }
 
@@ -43,6 +56,25 @@ __device__ __forceinline__ void sum_m1(const R s[Q], R m1[3])
         if (cy) m1[1] += cy * s[l];
         if (cz) m1[2] += cz * s[l];
     }
+}
+
+// A boundary node of the tile or ring: its populations from the boundary
+// rule, rho u into the ring buffer (stride between components js) and, when
+// sdst is given, the populations into the plane buffer (stride ss).  Out of
+// line so that the common interior path keeps its arrays in registers.
+template <class S, class R>
+__device__ __noinline__ void boundary_site(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                           const R* __restrict__ geo, int x, int y, int z, R* jdst, int js, R* sdst,
+                                           int ss)
+{
+    R s[Q], m1[3];
+    boundary_pops<S, R>(L, P, hist, geo, x, y, z, s);
+    sum_m1(s, m1);
+    const long long v = nidx(L, x, y, z);
+    const R sg = geo[v];
+    for (int a = 0; a < 3; a++) jdst[a * js] = sg * m1[a] + R(0.5) * hist[(1 + a) * L.N + v];
+    if (sdst)
+        for (int l = 0; l < Q; l++) sdst[l * ss] = s[l];
 }
 
 template <class S, class R>
@@ -77,7 +109,8 @@ __global__ void __launch_bounds__(FT, sizeof(R) == 4 ? 2 : 1)
     if (xout && xper) gx = wrapc(gx, n0);
     if (yout && yper) gy = wrapc(gy, n1);
 
-    // rho u of plane zz at the tile and ring sites (and the tile's populations)
+    // rho u of plane zz at the tile and ring sites (and the tile's populations);
+    // the loads of both sites are issued before either is used
     auto gather_plane = [&](int zz, int buf, bool keep) {
         int zw = zz;
         if (zz < 0 || zz >= n2) {
@@ -85,27 +118,35 @@ __global__ void __launch_bounds__(FT, sizeof(R) == 4 ? 2 : 1)
             zw = wrapc(zz, n2);
         }
         const int sl = pslot(zz);
-        if (active) {
-            R s[Q], m1[3];
-            node_pops<S, R>(L, Pin, hin, geo, x, y, zw, s);
-            sum_m1(s, m1);
+        const bool di = active, dr = has_ring && !rghost;
+        const bool bi = di && on_boundary(L, x, y, zw), br = dr && on_boundary(L, gx, gy, zw);
+        R si[Q], sr[Q];
+        const bool fi = di && !bi, fr = dr && !br;
+        if (fi) gather_raw<S, R>(L, Pin, x, y, zw, si);
+        if (fr) gather_raw<S, R>(L, Pin, gx, gy, zw, sr);
+        if (fi) {
+            R m1[3];
+            sum_m1(si, m1);
             const long long v = nidx(L, x, y, zw);
             const R sg = __ldg(geo + v);
 #pragma unroll
             for (int a = 0; a < 3; a++) sm.j[sl][a][ty + 1][tx + 1] = sg * m1[a] + R(0.5) * __ldg(hin + (1 + a) * N + v);
             if (keep)
 #pragma unroll
-                for (int l = 0; l < Q; l++) sm.s[buf][l][ty][tx] = s[l];
+                for (int l = 0; l < Q; l++) sm.s[buf][l][ty][tx] = si[l];
         }
-        if (has_ring && !rghost) {
-            R s[Q], m1[3];
-            node_pops<S, R>(L, Pin, hin, geo, gx, gy, zw, s);
-            sum_m1(s, m1);
+        if (fr) {
+            R m1[3];
+            sum_m1(sr, m1);
             const long long v = nidx(L, gx, gy, zw);
             const R sg = __ldg(geo + v);
 #pragma unroll
             for (int a = 0; a < 3; a++) sm.j[sl][a][ry][rx] = sg * m1[a] + R(0.5) * __ldg(hin + (1 + a) * N + v);
         }
+        if (bi)
+            boundary_site<S, R>(L, Pin, hin, geo, x, y, zw, &sm.j[sl][0][ty + 1][tx + 1], EY * EX,
+                                keep ? &sm.s[buf][0][ty][tx] : nullptr, FY * FX);
+        if (br) boundary_site<S, R>(L, Pin, hin, geo, gx, gy, zw, &sm.j[sl][0][ry][rx], EY * EX, nullptr, 0);
     };
 
     // ring sites outside a non-periodic x or y face of an in-domain plane
@@ -153,6 +194,16 @@ __global__ void __launch_bounds__(FT, sizeof(R) == 4 ? 2 : 1)
 
     for (int z = z0; z < z1; z++) {
         const int cur = (z - z0) & 1;
+        // geometry and history of the plane stepped below, copied while the
+        // next plane is gathered (each thread reads back only its own node)
+        if (active) {
+            const long long v = nidx(L, x, y, z);
+#pragma unroll
+            for (int k = 0; k < NGEO; k++) cp_async(&sm.geo[k][ty][tx], geo + k * N + v);
+#pragma unroll
+            for (int k = 0; k < NHIST; k++) cp_async(&sm.hist[k][ty][tx], hin + k * N + v);
+            cp_async_commit();
+        }
         gather_plane(z + 1, cur ^ 1, z + 1 < z1);
         __syncthreads();
         fill_xy_ghosts(z + 1);
@@ -164,10 +215,22 @@ __global__ void __launch_bounds__(FT, sizeof(R) == 4 ? 2 : 1)
         }
         if (active) {
             const long long v = nidx(L, x, y, z);
+            cp_async_wait_all();
             Geo<R> G;
-            load_geo(geo, N, v, G);
+            G.sg = sm.geo[0][ty][tx];
+            G.isg = R(1) / G.sg;
+#pragma unroll
+            for (int a = 0; a < 6; a++) G.gi[a] = sm.geo[1 + a][ty][tx];
+#pragma unroll
+            for (int a = 0; a < 18; a++) G.gam[a] = sm.geo[7 + a][ty][tx];
+#pragma unroll
+            for (int k = 0; k < 3; k++) G.gc[k] = G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)] + G.gam[2 * 6 + s6(k, 2)];
             Hist<R> Hp;
-            load_hist(hin, N, v, Hp);
+            Hp.A = sm.hist[0][ty][tx];
+#pragma unroll
+            for (int a = 0; a < 3; a++) Hp.B[a] = sm.hist[1 + a][ty][tx];
+#pragma unroll
+            for (int a = 0; a < 6; a++) Hp.C[a] = sm.hist[4 + a][ty][tx];
             R s[Q];
 #pragma unroll
             for (int l = 0; l < Q; l++) s[l] = sm.s[cur][l][ty][tx];

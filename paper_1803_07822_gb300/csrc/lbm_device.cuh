@@ -247,21 +247,26 @@ __device__ __forceinline__ void sums(const R s[Q], R& m0, R m1[3], R m2[6])
     }
 }
 
-// Node state: shifted populations s = h - w of the node together with its
-// geometry sums.  For a boundary node the populations come from the boundary
-// rule applied to its inner node (non-equilibrium extrapolation for wall and
-// inflow nodes, zero-gradient copy for outflow nodes, both scaled by
-// sqrt(g_inner)/sqrt(g_node)); h is then f - F'/2 with the node's own history.
+// Is the node on a non-periodic face?
+__device__ __forceinline__ bool on_boundary(const Lat& L, int x, int y, int z)
+{
+    return (L.bclo[0] != BC_PERIODIC && (x == 0 || x == L.n[0] - 1)) ||
+           (L.bclo[1] != BC_PERIODIC && (y == 0 || y == L.n[1] - 1)) ||
+           (L.bclo[2] != BC_PERIODIC && (z == 0 || z == L.n[2] - 1));
+}
+
+// Populations s = h - w of a boundary node from the boundary rule applied to
+// its inner node: non-equilibrium extrapolation for wall and inflow nodes,
+// zero-gradient copy for outflow nodes, both scaled by sqrt(g_inner) /
+// sqrt(g_node); h is then f - F'/2 with the node's own history.  Kept out of
+// line where it matters (see boundary_site): it runs for the few nodes on the
+// faces.
 template <class S, class R>
-__device__ __forceinline__ void node_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
-                                          const R* __restrict__ geo, int x, int y, int z, R s[Q])
+__device__ __forceinline__ void boundary_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                           const R* __restrict__ geo, int x, int y, int z, R s[Q])
 {
     int r[3] = {x, y, z}, in[3], axis = 0, side = 0;
-    int bc = classify(L, r, axis, side, in);
-    if (bc == BC_PERIODIC) {
-        gather_raw<S, R>(L, P, x, y, z, s);
-        return;
-    }
+    const int bc = classify(L, r, axis, side, in);
     const long long N = L.N;
     const long long vw = nidx(L, x, y, z), vi = nidx(L, in[0], in[1], in[2]);
     R si[Q];
@@ -273,7 +278,6 @@ __device__ __forceinline__ void node_pops(const Lat& L, const S* __restrict__ P,
     load_hist(hist, N, vi, Hi);
     load_hist(hist, N, vw, Hw);
     const R ratio = Gi.sg * Gw.isg;
-    // f at the inner node
     R fi[Q];
 #pragma unroll
     for (int l = 0; l < Q; l++) fi[l] = si[l] + R(wq(l)) + R(0.5) * forcing_l(l, Gi.isg, Hi);
@@ -308,6 +312,16 @@ __device__ __forceinline__ void node_pops(const Lat& L, const S* __restrict__ P,
         R fw = few + (fi[l] - fei) * ratio;
         s[l] = fw - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
     }
+}
+
+// Node state: shifted populations s = h - w of any node (boundary nodes
+// through the boundary rule).
+template <class S, class R>
+__device__ __forceinline__ void node_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                          const R* __restrict__ geo, int x, int y, int z, R s[Q])
+{
+    if (on_boundary(L, x, y, z)) boundary_pops<S, R>(L, P, hist, geo, x, y, z, s);
+    else gather_raw<S, R>(L, P, x, y, z, s);
 }
 
 // Momentum field value at a stencil site that may lie one step outside the

@@ -9,9 +9,10 @@ Conventions: a field on an (n0, n1, n2) lattice is an array [components, N]
 with node = x + n0*(y + n1*z) (axis 0 fastest).  J9[a*3+i] = d h^a / d x^i.
 g6 holds g_00, g_01, g_02, g_11, g_12, g_22; dg18[k*6+ij] = d_k g_ij.
 
-Channel layout used by all workloads: axis 0 is wall-normal (walls at
-x = 0 and x = n0-1; the x = 0 wall is fixed), axis 1 is the span (periodic),
-axis 2 is the flow direction.
+Channel layout: a channel is described by (wall, span, flow) axes.  The
+default layout puts the wall-normal direction on axis 2 (walls at x2 = 0 and
+x2 = n2-1; the x2 = 0 wall is fixed), the flow direction on axis 1 and the
+periodic span on axis 0.
 """
 from __future__ import annotations
 
@@ -97,18 +98,24 @@ class Deformation:
         return Deformation(*(a * v for v in (self.d, self.dp, self.ds, self.dpp, self.dps, self.dss)))
 
 
+LAYOUT = (2, 0, 1)  # (wall-normal axis, span axis, flow axis)
+
+
 def fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, kmax=4, lmax=3,
-                        coeffs=None, modes=None):
+                        coeffs=None, modes=None, layout=LAYOUT):
     """d = amp * H * D / max|D| with D = sum_m c_m cos(2 pi k_m s/L_s + 2 pi l_m p/L_p + phi_m);
-    on a non-periodic flow axis d is tapered by sin^2(pi s/(n2-1)) so that the
-    inlet and outlet stay flat.  c_m ~ N(0,1), k_m in 1..kmax, l_m in 0..lmax,
+    on a non-periodic flow axis d is tapered by sin^2(pi s/(n_flow-1)) so that
+    the inlet and outlet stay flat.  p and s are the span and flow coordinates
+    of ``layout`` = (wall, span, flow) axes; H = n_wall - 1.  c_m ~ N(0,1), k_m in 1..kmax, l_m in 0..lmax,
     phi_m ~ U[0, 2 pi), all from numpy's default_rng(seed).  When ``coeffs`` and
     ``modes`` are given they replace the draws (``amp`` is then an absolute
     scale: d = amp * H * D)."""
-    _, p, s = grid(n)
-    H = n[0] - 1
-    Ls = n[2] if flow_periodic else n[2] - 1
-    Lp = n[1]
+    ax_w, ax_p, ax_s = layout
+    r = grid(n)
+    p, s = r[ax_p], r[ax_s]
+    H = n[ax_w] - 1
+    Ls = n[ax_s] if flow_periodic else n[ax_s] - 1
+    Lp = n[ax_p]
     if modes is None:
         rng = np.random.default_rng(seed)
         k = rng.integers(1, kmax + 1, size=n_modes)
@@ -135,7 +142,7 @@ def fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, kmax=4, lmax=
     if flow_periodic:
         S, S1, S2 = np.ones_like(s), np.zeros_like(s), np.zeros_like(s)
     else:
-        w = np.pi / (n[2] - 1)
+        w = np.pi / (n[ax_s] - 1)
         S = np.sin(w * s) ** 2
         S1 = w * np.sin(2.0 * w * s)
         S2 = 2.0 * w * w * np.cos(2.0 * w * s)
@@ -143,26 +150,31 @@ def fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, kmax=4, lmax=
                        K * (Dps * S + Dp * S1), K * (Dss * S + 2.0 * Ds * S1 + D * S2))
 
 
-def channel_chart(n, dfm: Deformation):
-    """Exterior linear interpolation between the fixed wall x = 0 and the
-    displaced wall x = H (Sec. IV.A position coupling, case (i)):
-    h(x, p, s) = (x (1 + d(p,s)/H), p, s)."""
-    x, _, _ = grid(n)
-    H = n[0] - 1
-    N = x.size
+def channel_chart(n, dfm: Deformation, layout=LAYOUT):
+    """Exterior linear interpolation between the fixed wall x_w = 0 and the
+    displaced wall x_w = H (Sec. IV.A position coupling, case (i)):
+    h^w = x_w (1 + d(p,s)/H), the other components the identity."""
+    w, a_p, a_s = layout
+    r = grid(n)
+    xw = r[w]
+    H = n[w] - 1
+    N = xw.size
     J9 = np.zeros((9, N))
-    J9[0] = 1.0 + dfm.d / H
-    J9[1] = x * dfm.dp / H
-    J9[2] = x * dfm.ds / H
-    J9[4] = 1.0
-    J9[8] = 1.0
+    J9[[0, 4, 8]] = 1.0
+    J9[w * 3 + w] = 1.0 + dfm.d / H
+    J9[w * 3 + a_p] = xw * dfm.dp / H
+    J9[w * 3 + a_s] = xw * dfm.ds / H
     hess = np.zeros((27, N))
-    # d_j d_k h^0
-    hess[0 * 9 + 0 * 3 + 1] = hess[0 * 9 + 1 * 3 + 0] = dfm.dp / H
-    hess[0 * 9 + 0 * 3 + 2] = hess[0 * 9 + 2 * 3 + 0] = dfm.ds / H
-    hess[0 * 9 + 1 * 3 + 1] = x * dfm.dpp / H
-    hess[0 * 9 + 1 * 3 + 2] = hess[0 * 9 + 2 * 3 + 1] = x * dfm.dps / H
-    hess[0 * 9 + 2 * 3 + 2] = x * dfm.dss / H
+
+    def put(j, k, val):  # d_j d_k h^w
+        hess[w * 9 + j * 3 + k] = val
+        hess[w * 9 + k * 3 + j] = val
+
+    put(w, a_p, dfm.dp / H)
+    put(w, a_s, dfm.ds / H)
+    put(a_p, a_p, xw * dfm.dpp / H)
+    put(a_p, a_s, xw * dfm.dps / H)
+    put(a_s, a_s, xw * dfm.dss / H)
     return Chart(tuple(n), J9, hess)
 
 
@@ -181,24 +193,26 @@ def contravariant(J9, v3, nodes):
     return np.linalg.solve(J, v3.T[..., None])[..., 0].T
 
 
-def wall_velocity(n, chart: Chart, dfm_rate: Deformation):
-    """Contravariant velocity of the top wall (x = n0-1) moving with d'(t):
-    Cartesian v = (dd/dt, 0, 0), u = J^-1 v."""
-    nodes = face_nodes(n, 0, 1)
+def wall_velocity(n, chart: Chart, dfm_rate: Deformation, layout=LAYOUT):
+    """Contravariant velocity of the displaced wall (x_w = n_w - 1) moving with
+    d'(t): Cartesian v = dd/dt along the wall normal, u = J^-1 v."""
+    w = layout[0]
+    nodes = face_nodes(n, w, 1)
     v = np.zeros((3, nodes.size))
-    v[0] = dfm_rate.d[nodes]
+    v[w] = dfm_rate.d[nodes]
     return contravariant(chart.J9, v, nodes)
 
 
-def inflow_profile(n, chart: Chart, umax):
-    """Parabolic inflow on face (axis 2, low): Cartesian v_flow =
+def inflow_profile(n, chart: Chart, umax, layout=LAYOUT):
+    """Parabolic inflow on face (flow axis, low): Cartesian v_flow =
     4 umax xc (H - xc) / H^2 with xc the Cartesian wall-normal position."""
-    nodes = face_nodes(n, 2, 0)
-    x, _, _ = grid(n)
-    H = n[0] - 1
-    xc = x[nodes] * chart.J9[0, nodes]  # h^0 = x (1 + d/H) and J^0_0 = 1 + d/H
+    w, _, a_s = layout
+    nodes = face_nodes(n, a_s, 0)
+    xw = grid(n)[w]
+    H = n[w] - 1
+    xc = xw[nodes] * chart.J9[w * 3 + w, nodes]  # h^w = x_w (1 + d/H), J^w_w = 1 + d/H
     v = np.zeros((3, nodes.size))
-    v[2] = 4.0 * umax * xc * (H - xc) / (H * H)
+    v[a_s] = 4.0 * umax * xc * (H - xc) / (H * H)
     return contravariant(chart.J9, v, nodes)
 
 
@@ -226,46 +240,60 @@ def time_law(t, period=2000.0):
 WALL, PERIODIC, INFLOW, OUTFLOW = 1, 0, 2, 3
 
 
-def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None):
-    """Walls across axis 0, periodic span and flow, body-force drive along
-    axis 2 with centre-line speed umax."""
+def _bcs(layout, flow_rule_lo, flow_rule_hi):
+    lo, hi = [PERIODIC] * 3, [PERIODIC] * 3
+    w, _, a_s = layout
+    lo[w] = hi[w] = WALL
+    lo[a_s], hi[a_s] = flow_rule_lo, flow_rule_hi
+    return tuple(lo), tuple(hi)
+
+
+def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None, layout=LAYOUT):
+    """Walls across the wall axis, periodic span and flow, body-force drive
+    along the flow axis with centre-line speed umax."""
     nu = (tau - 0.5) / 3.0
-    H = n[0] - 1
-    dfm = fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, modes=modes,
-                              coeffs=coeffs)
-    return dict(n=tuple(n), bc_lo=(WALL, PERIODIC, PERIODIC), bc_hi=(WALL, PERIODIC, PERIODIC),
-                tau=tau, fext=(0.0, 0.0, body_force(nu, umax, H)), dfm=dfm,
-                chart=channel_chart(n, dfm), faces={})
+    w, _, a_s = layout
+    H = n[w] - 1
+    dfm = fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, modes=modes, coeffs=coeffs,
+                              layout=layout)
+    lo, hi = _bcs(layout, PERIODIC, PERIODIC)
+    fext = [0.0, 0.0, 0.0]
+    fext[a_s] = body_force(nu, umax, H)
+    return dict(n=tuple(n), bc_lo=lo, bc_hi=hi, tau=tau, fext=tuple(fext), dfm=dfm,
+                chart=channel_chart(n, dfm, layout), faces={}, layout=layout, wall_axis=w)
 
 
-def plain_fp64_channel(n=(16, 16, 32)):
-    """Static one-mode channel: d = 0.05 H sin(2 pi s / n2), tau = 0.8,
-    body force for umax = 0.05 (the first workload of the plain method)."""
+def plain_fp64_channel(n=(16, 32, 16), layout=LAYOUT):
+    """Static one-mode channel (16 x 16 x 32 nodes, 32 along the flow):
+    d = 0.05 H sin(2 pi s / n_flow), tau = 0.8, body force for umax = 0.05."""
     return periodic_channel(n, 0.8, 0.05, 1, 0.05, 0, modes=([1], [0], [-np.pi / 2]),
-                            coeffs=[1.0])
+                            coeffs=[1.0], layout=layout)
 
 
-def dynamic_channel(n=(128, 128, 256), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
-                    t=0.0, period=2000.0, kmax=4, lmax=3):
-    """Walls across axis 0, periodic span, parabolic inflow at z = 0 and
-    outflow at z = n2-1; deformation scaled by a(t) = sin^2(pi t/period)."""
+def dynamic_channel(n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
+                    t=0.0, period=2000.0, kmax=4, lmax=3, layout=LAYOUT):
+    """Walls across the wall axis, periodic span, parabolic inflow at the low
+    flow face and outflow at the high one; deformation scaled by
+    a(t) = sin^2(pi t/period)."""
     nu = (tau - 0.5) / 3.0
-    H = n[0] - 1
+    w = layout[0]
+    H = n[w] - 1
     umax = re * nu / H
-    base = fourier_deformation(n, n_modes, amp, seed, flow_periodic=False, kmax=kmax, lmax=lmax)
-    a, adot = time_law(t, period)
-    dfm = base.scaled(a)
-    chart = channel_chart(n, dfm)
-    faces = {(2, 0): inflow_profile(n, chart, umax), (0, 1): wall_velocity(n, chart, base.scaled(adot))}
-    return dict(n=tuple(n), bc_lo=(WALL, PERIODIC, INFLOW), bc_hi=(WALL, PERIODIC, OUTFLOW),
-                tau=tau, fext=(0.0, 0.0, 0.0), dfm=dfm, base=base, chart=chart, faces=faces,
-                umax=umax, period=period)
+    base = fourier_deformation(n, n_modes, amp, seed, flow_periodic=False, kmax=kmax, lmax=lmax,
+                               layout=layout)
+    lo, hi = _bcs(layout, INFLOW, OUTFLOW)
+    wl = dict(n=tuple(n), bc_lo=lo, bc_hi=hi, tau=tau, fext=(0.0, 0.0, 0.0), base=base, umax=umax,
+              period=period, layout=layout, wall_axis=w)
+    wl["chart"], wl["faces"] = dynamic_channel_at(wl, t)
+    wl["dfm"] = base.scaled(time_law(t, period)[0])
+    return wl
 
 
 def dynamic_channel_at(w, t):
     """The chart and face velocities of a dynamic_channel workload at time t."""
     a, adot = time_law(t, w["period"])
-    chart = channel_chart(w["n"], w["base"].scaled(a))
-    faces = {(2, 0): inflow_profile(w["n"], chart, w["umax"]),
-             (0, 1): wall_velocity(w["n"], chart, w["base"].scaled(adot))}
+    lay = w["layout"]
+    chart = channel_chart(w["n"], w["base"].scaled(a), lay)
+    faces = {(lay[2], 0): inflow_profile(w["n"], chart, w["umax"], lay),
+             (lay[0], 1): wall_velocity(w["n"], chart, w["base"].scaled(adot), lay)}
     return chart, faces

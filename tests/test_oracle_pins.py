@@ -126,8 +126,9 @@ def test_sqrtg_derivative_identity_converges():
     errs = []
     for n2 in (32, 64):
         n = (5, 4, n2)
-        dfm = I.fourier_deformation(n, 3, 0.08, seed=5, flow_periodic=True, kmax=2)
-        ch = I.channel_chart(n, dfm)
+        lay = (0, 1, 2)  # flow along axis 2
+        dfm = I.fourier_deformation(n, 3, 0.08, seed=5, flow_periodic=True, kmax=2, layout=lay)
+        ch = I.channel_chart(n, dfm, lay)
         sg, _, gam = oracle.geometry(n, ch.g6, ch.dg18)
         s3 = sg.reshape(n2, 4, 5)
         G = gam.reshape(3, 3, 3, -1)

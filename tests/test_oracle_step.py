@@ -134,18 +134,18 @@ def test_rest_wall_force_is_pressure_times_area():
     """At rest with uniform rho, T = rho theta g^-1 on the wall nodes, so the
     force on a wall is p * sum (e_j x e_k) over its nodes (the Cartesian area
     vector of the deformed wall, from the chart's tangent vectors)."""
-    n = (9, 8, 12)
+    n = (8, 12, 9)
     dfm = I.fourier_deformation(n, 4, 0.08, seed=21, flow_periodic=True)
     ch = I.channel_chart(n, dfm)
-    L = oracle.Lattice(n, (W, P, P), (W, P, P), tau=0.8)
+    L = oracle.Lattice(n, (P, P, W), (P, P, W), tau=0.8)
     L.set_metric(ch.g6, ch.dg18)
     L.init()
     J = ch.J9.reshape(3, 3, -1)
     p = 1.0 / 3.0
     for side in (0, 1):
-        nodes = I.face_nodes(n, 0, side)
-        area = np.cross(J[:, 1, nodes].T, J[:, 2, nodes].T).sum(0)
-        F = L.wall_force(0, side, ch.J9)
+        nodes = I.face_nodes(n, 2, side)
+        area = np.cross(J[:, 0, nodes].T, J[:, 1, nodes].T).sum(0)
+        F = L.wall_force(2, side, ch.J9)
         s = 1.0 if side else -1.0
         assert np.allclose(F, s * p * area, rtol=0, atol=1e-12)
 
@@ -245,9 +245,10 @@ def test_curved_rest_spurious_velocity_small_and_shrinking():
     peaks = []
     for s in (1, 2):
         n = (8 * s + 1, 1, 16 * s)
+        lay = (0, 1, 2)  # walls across axis 0, flow along axis 2
         dfm = I.fourier_deformation(n, 1, 0.05, 0, True, modes=([1], [0], [-np.pi / 2]),
-                                    coeffs=[1.0])
-        ch = I.channel_chart(n, dfm)
+                                    coeffs=[1.0], layout=lay)
+        ch = I.channel_chart(n, dfm, lay)
         L = oracle.Lattice(n, (W, P, P), (W, P, P), tau=0.8)
         L.set_metric(ch.g6, ch.dg18)
         L.init()
