@@ -3,6 +3,7 @@
 // kernels themselves live in kernels.cuh (one instantiation per format).
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -68,7 +69,9 @@ cslbm_status validate(const cslbm_params* p)
     }
     if (!(p->tau > 0.5)) return fail(CSLBM_EINVAL, "tau must exceed 1/2");
     if (!ops_for(p->storage)) return fail(CSLBM_EINVAL, "unknown storage format");
-    if ((long long)p->n[0] * p->n[1] * p->n[2] > (1LL << 40)) return fail(CSLBM_EINVAL, "lattice too large");
+    // the step kernel indexes fields with 32-bit offsets (25 components of N)
+    if (25LL * p->n[0] * p->n[1] * p->n[2] >= (1LL << 32))
+        return fail(CSLBM_EINVAL, "lattice too large: at most 171,798,691 nodes per context");
     return CSLBM_OK;
 }
 
@@ -84,7 +87,7 @@ Layout layout(const cslbm_params* p)
     for (int k = 0; k < 2; k++) { L.off_H[k] = o; o += al(10 * L.N * L.r_bytes); }
     for (int k = 0; k < 2; k++) { L.off_G[k] = o; o += al(25 * L.N * L.r_bytes); }
     L.off_J = o; o += al(9 * L.N * sizeof(double));
-    L.off_jf = o; o += al(3 * L.N * L.r_bytes);
+    L.off_jf = o; o += al(4 * L.N * L.r_bytes);
     for (int k = 0; k < 6; k++) {
         int a = k / 2;
         bool periodic = (k & 1 ? p->bc_hi[a] : p->bc_lo[a]) == CSLBM_PERIODIC;
@@ -140,6 +143,41 @@ cslbm_status stage_in(cslbm_ctx* c, const double* src, int ncomp, long long v0, 
         CUDA_TRY(cudaMemcpyAsync(dst + k * cnt, src + k * c->N + v0, cnt * sizeof(double), cudaMemcpyDefault,
                                  c->stream));
     return CSLBM_OK;
+}
+
+// Tensor maps of the geometry [25][N] and history [10][N] buffers viewed as
+// 4-D (x, y, z, component) arrays with a 32 x 8 x 1 x all-components box,
+// for the bulk-copy step.  Returns false when they cannot be made (the
+// general step kernel is used then).
+bool make_tensor_maps(cslbm_ctx* c)
+{
+    if (c->p.storage != CSLBM_FP32 || c->n[0] % 32 || c->n[1] % 8) return false;
+    typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn ||
+        q != cudaDriverEntryPointSuccess)
+        return false;
+    encode_fn encode = (encode_fn)fn;
+    const cuuint64_t n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    for (int k = 0; k < 2; k++) {
+        for (int which = 0; which < 2; which++) {
+            const cuuint64_t comps = which ? 10 : 25;
+            const cuuint64_t dims[4] = {n0, n1, n2, comps};
+            const cuuint64_t strides[3] = {n0 * 4, n0 * n1 * 4, n0 * n1 * n2 * 4};
+            const cuuint32_t box[4] = {32, 8, 1, (cuuint32_t)comps};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUtensorMap* m = which ? &c->tm_hist[k] : &c->tm_geo[k];
+            void* base = which ? c->H[k] : c->G[k];
+            if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
+    }
+    return true;
 }
 
 cslbm_status read_scratch(cslbm_ctx* c, double* out, int k)
@@ -233,6 +271,8 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
     c->pc = c->hc = c->gc = 0;
     c->has_state = 0;
     c->ops = ops_for(p->storage);
+    c->use_tma = make_tensor_maps(c) ? 1 : 0;
+    { const char* e = getenv("CSLBM_STEP"); c->step_kind = e ? atoi(e) : 0; }
     cslbm_status s = CSLBM_OK;
     if (cudaMemsetAsync(ws, 0, L.total, c->stream) != cudaSuccess) s = fail(CSLBM_ECUDA, "workspace memset failed");
     if (!s) s = set_flat(c, 0);
@@ -365,7 +405,7 @@ cslbm_status cslbm_step(cslbm_ctx* c, int nsteps)
             CUDA_TRY(cudaEventRecord(e[0], c->stream));
         }
         c->ops->step(c, 0);
-        c->launches += 1;
+        c->launches += c->step_kind == 1 ? 2 : 1;
         LAUNCH_CHECK("step kernel");
         if (c->prof) {
             CUDA_TRY(cudaEventRecord(c->ev.back(), c->stream));
@@ -438,6 +478,9 @@ cslbm_status cslbm_check(cslbm_ctx* c)
     LAUNCH_CHECK("check kernel");
     double bad = 0.0;
     if (cslbm_status s = read_scratch(c, &bad, 1)) return s;
+    int tmo = 0;
+    CUDA_TRY(cudaMemcpy(&tmo, c->scratch + 40, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) return fail(CSLBM_ETIMEOUT, "a bounded wait of the step kernel ran out (copy engine stalled)");
     if (bad > 0.0) {
         char m[96];
         snprintf(m, sizeof m, "%.0f nodes with non-finite density or |v| > 0.3", bad);

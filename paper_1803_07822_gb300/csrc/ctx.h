@@ -2,6 +2,7 @@
 // per-storage-format kernel units.  Not part of the public interface.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -24,7 +25,7 @@ struct cslbm_ctx {
     void* H[2];      // [10][N] forcing-history coefficients
     void* G[2];      // [25][N] geometry: sqrt(g), g^ij, Gamma
     double* J;       // [9][N] current chart Jacobian (FP64)
-    void* jf;        // [3][N] momentum field (initial forcing only)
+    void* jf;        // [N] rho u (x, y, z, unused) of every node
     double* face[6]; // [3][face nodes] boundary velocity of non-periodic faces
     long long face_n[6];
     double* scratch; // 64 doubles of reduction space
@@ -34,6 +35,12 @@ struct cslbm_ctx {
     int has_state;
     int metric_check_pending;  // a metric kernel ran without a host check
     const cslbm_ops* ops;
+    // tensor maps of the geometry and history buffers for the bulk-copy step
+    // (FP32 storage, n0 % 32 == 0, n1 % 8 == 0)
+    int use_tma;
+    int step_kind;  // experiment: 0 fused, 1 flat, 2 staged
+    CUtensorMap tm_geo[2];
+    CUtensorMap tm_hist[2];
     // profiling
     int prof;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of profiled steps

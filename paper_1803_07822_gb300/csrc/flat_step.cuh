@@ -1,0 +1,252 @@
+// LBM step as two flat passes per time step.
+//
+// The forcing moment C^ij (Eq. forcing-C) needs the lattice gradient of
+// rho u at time t on the 18 neighbours of every node (App. D).  The first
+// pass forms rho u of every node (one float4 per node, a field small enough
+// to stay in L2); the second pass steps every node independently: pull
+// gather, moments, stress, gradient from the neighbours' rho u, forcing
+// moments, collision, store.  No barriers and no shared memory, so the SMs
+// run at the occupancy the registers allow; the price over the one-pass
+// ideal is one extra read of the populations per step.
+//
+// Nodes on a non-periodic face take one generic out-of-line path (boundary
+// rule, ghost extrapolation of the stencil); every other node has all its
+// pull sources and stencil sites inside the domain after periodic wrapping.
+#pragma once
+
+#include "step_math.cuh"
+
+namespace cslbm {
+
+template <class R> struct alignas(4 * sizeof(R)) Mom4 {
+    R x, y, z, w;
+};
+
+// 32-bit element offsets of a node's pull sources / stencil sites for
+// c in {-1, 0, +1} per axis (the host guarantees 25 N < 2^32)
+struct Nbr {
+    unsigned xs[3], ys[3], zs[3];
+};
+__device__ __forceinline__ Nbr nbr_index(const Lat& L, int x, int y, int z, int sign)
+{
+    Nbr p;
+    const unsigned n0 = L.n[0], n01 = (unsigned)L.n[0] * L.n[1];
+#pragma unroll
+    for (int c = -1; c <= 1; c++) {
+        p.xs[c + 1] = (unsigned)wrapc(x + sign * c, L.n[0]);
+        p.ys[c + 1] = (unsigned)wrapc(y + sign * c, L.n[1]) * n0;
+        p.zs[c + 1] = (unsigned)wrapc(z + sign * c, L.n[2]) * n01;
+    }
+    return p;
+}
+__device__ __forceinline__ unsigned nbr_off(const Nbr& p, int cx, int cy, int cz)
+{
+    return p.zs[cz + 1] + p.ys[cy + 1] + p.xs[cx + 1];
+}
+
+// rho u of a boundary node from the boundary rule
+template <class S, class R>
+__device__ __noinline__ void momentum_boundary(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                               const R* __restrict__ geo, int x, int y, int z, Mom4<R>* jf)
+{
+    R s[Q];
+    boundary_pops<S, R>(L, P, hist, geo, x, y, z, s);
+    PairSums<R> Ps;
+    pair_sums(s, Ps);
+    R m1[3];
+    first_moment(Ps, m1);
+    const long long v = nidx(L, x, y, z);
+    const R sg = geo[v];
+    Mom4<R> j;
+    j.x = fmad(sg, m1[0], R(0.5) * hist[1 * L.N + v]);
+    j.y = fmad(sg, m1[1], R(0.5) * hist[2 * L.N + v]);
+    j.z = fmad(sg, m1[2], R(0.5) * hist[3 * L.N + v]);
+    j.w = R(0);
+    jf[v] = j;
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(256) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                       const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
+{
+    const unsigned N = (unsigned)L.N;
+    const unsigned v = blockIdx.x * 256u + threadIdx.x;
+    if (v >= N) return;
+    const int x = (int)(v % (unsigned)L.n[0]);
+    const unsigned r = v / (unsigned)L.n[0];
+    const int y = (int)(r % (unsigned)L.n[1]), z = (int)(r / (unsigned)L.n[1]);
+    if (on_boundary(L, x, y, z)) {
+        momentum_boundary<S, R>(L, P, hist, geo, x, y, z, jf);
+        return;
+    }
+    const Nbr src = nbr_index(L, x, y, z, -1);
+    R s[Q];
+#pragma unroll
+    for (int l = 0; l < Q; l++)
+        s[l] = R(Store<S>::ld(P + (unsigned)l * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
+    PairSums<R> Ps;
+    pair_sums(s, Ps);
+    R m1[3];
+    first_moment(Ps, m1);
+    const R sg = __ldg(geo + v);
+    Mom4<R> j;
+    j.x = fmad(sg, m1[0], R(0.5) * __ldg(hist + 1 * N + v));
+    j.y = fmad(sg, m1[1], R(0.5) * __ldg(hist + 2 * N + v));
+    j.z = fmad(sg, m1[2], R(0.5) * __ldg(hist + 3 * N + v));
+    j.w = R(0);
+    jf[v] = j;
+}
+
+// rho u at a stencil site that may lie one step outside a non-periodic face:
+// linear extrapolation 2 j(face) - j(face - normal) per out-of-range axis
+template <class R>
+__device__ __forceinline__ Mom4<R> mom_site(const Lat& L, const Mom4<R>* __restrict__ jf, int x, int y, int z)
+{
+    int r[3] = {x, y, z}, c0[3], c1[3], nopt[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int n = L.n[a];
+        c1[a] = 0;
+        if (r[a] >= 0 && r[a] < n) { c0[a] = r[a]; nopt[a] = 1; }
+        else if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) { c0[a] = wrapc(r[a], n); nopt[a] = 1; }
+        else if (r[a] < 0) { c0[a] = 0; c1[a] = 1; nopt[a] = 2; }
+        else { c0[a] = n - 1; c1[a] = n - 2; nopt[a] = 2; }
+    }
+    Mom4<R> acc;
+    acc.x = acc.y = acc.z = acc.w = R(0);
+    for (int i = 0; i < nopt[0]; i++)
+        for (int k = 0; k < nopt[1]; k++)
+            for (int m = 0; m < nopt[2]; m++) {
+                const R wt = (i ? R(-1) : (nopt[0] == 2 ? R(2) : R(1))) * (k ? R(-1) : (nopt[1] == 2 ? R(2) : R(1))) *
+                             (m ? R(-1) : (nopt[2] == 2 ? R(2) : R(1)));
+                const Mom4<R> j = jf[nidx(L, i ? c1[0] : c0[0], k ? c1[1] : c0[1], m ? c1[2] : c0[2])];
+                acc.x += wt * j.x;
+                acc.y += wt * j.y;
+                acc.z += wt * j.z;
+            }
+    return acc;
+}
+
+// the step of one node from its populations s (h - w), geometry and history
+// at element offset v, and the rho u differences d across the nine opposite
+// stencil pairs; stores the new populations and forcing coefficients
+template <class S, class R>
+__device__ __forceinline__ void step_core(const Lat& L, const R s[Q], const GeoT<R>& G, const HistT<R>& Hp,
+                                          const R d[9][3], S* __restrict__ Pout, R* __restrict__ hout, unsigned v,
+                                          unsigned N)
+{
+    PairSums<R> Ps;
+    pair_sums(s, Ps);
+    R m0, m1[3], m2[6];
+    all_moments(s, Ps, m0, m1, m2);
+    const R rho = fmad(G.sg, m0 + R(1), R(0.5) * Hp.A);
+    const R ir = recip(rho);
+    R j[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) j[a] = fmad(G.sg, m1[a], R(0.5) * Hp.B[a]);
+    R Tt[6];
+    stress_t<R, R>(R(L.theta), R(L.kvisc), G, rho, ir, j, m2, Hp, Tt);
+    R D[3][3];
+    gradient_from_pairs(d, D);
+    const R fext[3] = {R(L.fext[0]), R(L.fext[1]), R(L.fext[2])};
+    HistT<R> H;
+    forcing_t<R, R>(R(L.theta), fext, G, j, Tt, D, H);
+    R out[Q];
+    collide_t<R, R>(R(L.omega), R(L.theta), G, s, m0, rho, ir, j, Hp, H, out);
+    hout[v] = H.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) hout[(1 + a) * N + v] = H.B[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) hout[(4 + a) * N + v] = H.C[a];
+#pragma unroll
+    for (int l = 0; l < Q; l++) Store<S>::st(Pout + (unsigned)l * N + v, out[l]);
+}
+
+template <class R>
+__device__ __forceinline__ void load_geo_hist(const R* __restrict__ geo, const R* __restrict__ hist, unsigned v,
+                                              unsigned N, GeoT<R>& G, HistT<R>& Hp)
+{
+    G.sg = __ldg(geo + v);
+    G.isg = recip(G.sg);
+#pragma unroll
+    for (int a = 0; a < 6; a++) G.gi[a] = __ldg(geo + (1 + a) * N + v);
+#pragma unroll
+    for (int a = 0; a < 18; a++) G.gam[a] = __ldg(geo + (7 + a) * N + v);
+#pragma unroll
+    for (int k = 0; k < 3; k++) G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
+    Hp.A = __ldg(hist + v);
+#pragma unroll
+    for (int a = 0; a < 3; a++) Hp.B[a] = __ldg(hist + (1 + a) * N + v);
+#pragma unroll
+    for (int a = 0; a < 6; a++) Hp.C[a] = __ldg(hist + (4 + a) * N + v);
+}
+
+// the step of a node on a non-periodic face (boundary rule, ghost stencil)
+template <class S, class R>
+__device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                           const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ geo,
+                                           const Mom4<R>* __restrict__ jf, int x, int y, int z)
+{
+    const unsigned N = (unsigned)L.N, v = (unsigned)nidx(L, x, y, z);
+    R s[Q];
+    boundary_pops<S, R>(L, Pin, hin, geo, x, y, z, s);
+    GeoT<R> G;
+    HistT<R> Hp;
+    load_geo_hist(geo, hin, v, N, G, Hp);
+    R d[9][3];
+    for (int k = 0; k < 9; k++) {
+        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        const Mom4<R> p = mom_site(L, jf, x + cx, y + cy, z + cz), m = mom_site(L, jf, x - cx, y - cy, z - cz);
+        d[k][0] = p.x - m.x;
+        d[k][1] = p.y - m.y;
+        d[k][2] = p.z - m.z;
+    }
+    step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(256, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                      const R* __restrict__ hin, R* __restrict__ hout,
+                                                      const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+{
+    const unsigned N = (unsigned)L.N;
+    const unsigned v = blockIdx.x * 256u + threadIdx.x;
+    if (v >= N) return;
+    const int x = (int)(v % (unsigned)L.n[0]);
+    const unsigned r = v / (unsigned)L.n[0];
+    const int y = (int)(r % (unsigned)L.n[1]), z = (int)(r / (unsigned)L.n[1]);
+    if (on_boundary(L, x, y, z)) {
+        step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
+        return;
+    }
+    const Nbr src = nbr_index(L, x, y, z, -1);
+    R s[Q];
+#pragma unroll
+    for (int l = 0; l < Q; l++)
+        s[l] = R(Store<S>::ld(Pin + (unsigned)l * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
+    GeoT<R> G;
+    HistT<R> Hp;
+    load_geo_hist(geo, hin, v, N, G, Hp);
+    const Nbr nb = nbr_index(L, x, y, z, +1);  // sites x + c
+    R d[9][3];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        const Mom4<R> p = jf[nbr_off(nb, cx, cy, cz)], m = jf[nbr_off(nb, -cx, -cy, -cz)];
+        d[k][0] = p.x - m.x;
+        d[k][1] = p.y - m.y;
+        d[k][2] = p.z - m.z;
+    }
+    step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
+}
+
+template <class S, class R>
+void launch_flat_step(const cslbm_ctx* c, const Lat& L, const S* Pin, S* Pout, const R* hin, R* hout, const R* geo)
+{
+    const unsigned nb = (unsigned)((c->N + 255) / 256);
+    Mom4<R>* jf = (Mom4<R>*)c->jf;
+    k_momentum_flat<S, R><<<nb, 256, 0, c->stream>>>(L, Pin, hin, geo, jf);
+    k_step_flat<S, R><<<nb, 256, 0, c->stream>>>(L, Pin, Pout, hin, hout, geo, jf);
+}
+
+}  // namespace cslbm

@@ -4,9 +4,17 @@
 #pragma once
 
 #include "ctx.h"
+#include "flat_step.cuh"
+#include "fused_step.cuh"
 #include "lbm_device.cuh"
 
 namespace cslbm {
+
+// bulk-copy step for FP32 storage on tile-aligned lattices (fused_tma.cuh)
+struct Lat;
+bool tma_eligible(const cslbm_ctx* c);
+void launch_tma_step(const cslbm_ctx* c, const Lat& L, const float* Pin, float* Pout, const float* hin, float* hout,
+                     const float* geo);
 
 constexpr int TPB = 256;
 
@@ -173,21 +181,6 @@ __device__ __forceinline__ void node_moments(const Lat& L, const S* __restrict__
     for (int a = 0; a < 3; a++) M.j[a] = sg * M.m1[a] + R(0.5) * M.Hp.B[a];
 }
 
-// momentum field rho u^i of the current state (Eq. fields2)
-template <class S, class R>
-__global__ void __launch_bounds__(TPB) k_momentum(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                  const R* __restrict__ geo, R* __restrict__ jf)
-{
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= L.N) return;
-    int x, y, z;
-    node_coords(L, v, x, y, z);
-    NodeMoments<S, R> M;
-    node_moments<S, R>(L, P, hist, geo, x, y, z, v, geo[v], M);
-#pragma unroll
-    for (int a = 0; a < 3; a++) jf[a * L.N + v] = M.j[a];
-}
-
 // ---------------------------------------------------------------------------
 // Pieces of the step shared by the fused step kernel and the initial forcing.
 // ---------------------------------------------------------------------------
@@ -248,10 +241,11 @@ __device__ __forceinline__ void store_hist(R* __restrict__ h, long long N, long 
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_forcing(Lat L, const S* __restrict__ P, const R* __restrict__ hin,
                                                  R* __restrict__ hout, const R* __restrict__ geo,
-                                                 const R* __restrict__ jf)
+                                                 const void* __restrict__ jfv)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= L.N) return;
+    const Mom4<R>* jf = (const Mom4<R>*)jfv;
     int x, y, z;
     node_coords(L, v, x, y, z);
     Geo<R> G;
@@ -269,11 +263,12 @@ __global__ void __launch_bounds__(TPB) k_forcing(Lat L, const S* __restrict__ P,
     for (int l = 1; l < Q; l++) {
         const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
         const R wl = R(3.0 * wq(l));
+        const Mom4<R> jn = mom_site<R>(L, jf, x + cx, y + cy, z + cz);
+        const R jv[3] = {jn.x, jn.y, jn.z};
         for (int i = 0; i < 3; i++) {
-            R jn = jsite<R>(L, jf, i, x + cx, y + cy, z + cz);
-            D[0][i] += (wl * cx) * jn;
-            D[1][i] += (wl * cy) * jn;
-            D[2][i] += (wl * cz) * jn;
+            D[0][i] += (wl * cx) * jv[i];
+            D[1][i] += (wl * cy) * jv[i];
+            D[2][i] += (wl * cz) * jv[i];
         }
     }
     Hist<R> H;
@@ -543,11 +538,6 @@ __global__ void __launch_bounds__(TPB) k_check(Lat L, const S* __restrict__ P, c
     block_reduce_add<1>(val, acc);
 }
 
-}  // namespace cslbm
-
-#include "fused_step.cuh"
-
-namespace cslbm {
 
 // ---------------------------------------------------------------------------
 // host launchers
@@ -570,16 +560,26 @@ template <class S, class R> struct Launch {
     }
     static void momentum_field(const cslbm_ctx* c)
     {
-        k_momentum<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
-                                                               (R*)c->jf);
+        k_momentum_flat<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                                    (Mom4<R>*)c->jf);
     }
     static void step(const cslbm_ctx* c, int force_only)
     {
         Lat L = make_lat(c);
         if (force_only) {
             k_forcing<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(L, P(c, c->pc), H(c, c->hc), H(c, 1 - c->hc),
-                                                                 G(c, c->gc), (const R*)c->jf);
+                                                                 G(c, c->gc), c->jf);
             return;
+        }
+        if (c->step_kind == 1) {
+            launch_flat_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
+            return;
+        }
+        if constexpr (sizeof(S) == 4 && sizeof(R) == 4) {
+            if (c->step_kind == 2 && tma_eligible(c)) {
+                launch_tma_step(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
+                return;
+            }
         }
         launch_fused_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
     }

@@ -324,35 +324,6 @@ __device__ __forceinline__ void node_pops(const Lat& L, const S* __restrict__ P,
     else gather_raw<S, R>(L, P, x, y, z, s);
 }
 
-// Momentum field value at a stencil site that may lie one step outside the
-// lattice: periodic axes wrap; outside a non-periodic face the value is the
-// linear extrapolation 2 j(face) - j(face - normal), axis by axis.
-template <class R>
-__device__ __forceinline__ R jsite(const Lat& L, const R* __restrict__ jf, int comp, int x, int y, int z)
-{
-    int r[3] = {x, y, z};
-    int c0[3], c1[3];
-    R w0[3], w1[3];
-    int nopt[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const int n = L.n[a];
-        if (r[a] >= 0 && r[a] < n) { c0[a] = r[a]; w0[a] = R(1); nopt[a] = 1; c1[a] = 0; w1[a] = R(0); }
-        else if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) {
-            c0[a] = wrapc(r[a], n); w0[a] = R(1); nopt[a] = 1; c1[a] = 0; w1[a] = R(0);
-        } else if (r[a] < 0) { c0[a] = 0; w0[a] = R(2); c1[a] = 1; w1[a] = R(-1); nopt[a] = 2; }
-        else { c0[a] = n - 1; w0[a] = R(2); c1[a] = n - 2; w1[a] = R(-1); nopt[a] = 2; }
-    }
-    R acc = R(0);
-    for (int i = 0; i < nopt[0]; i++)
-        for (int k = 0; k < nopt[1]; k++)
-            for (int m = 0; m < nopt[2]; m++) {
-                R wt = (i ? w1[0] : w0[0]) * (k ? w1[1] : w0[1]) * (m ? w1[2] : w0[2]);
-                acc += wt * jf[comp * L.N + nidx(L, i ? c1[0] : c0[0], k ? c1[1] : c0[1], m ? c1[2] : c0[2])];
-            }
-    return acc;
-}
-
 // ---------------------------------------------------------------------------
 // forcing moments (Eqs. forcing-A/B/C), in terms of the contracted symbol
 // Gamma^j_kj =: gc_k (Gamma is symmetric in its lower indices):

@@ -215,3 +215,51 @@ def test_host_and_device_inputs_agree_and_state_roundtrip():
     r2, u2 = a.moments()
     assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
     assert a.check()
+
+
+# Lattices with n0 % 32 == 0 and n1 % 8 == 0 take the bulk-copy step kernel
+# (FP32 storage); the cases cover one x-tile (both periodic wraps in one
+# CTA), two x-tiles, walls across x, walls across z and inflow/outflow.
+TILED = [
+    ("span-x one tile", (32, 24, 12), (2, 0, 1), "inout"),
+    ("span-x two tiles", (64, 16, 9), (2, 0, 1), "inout"),
+    ("walls across x", (32, 16, 40), (0, 1, 2), "inout"),
+    ("periodic flow", (32, 32, 16), (2, 0, 1), "periodic"),
+]
+
+
+def smooth_wall_velocity(n, layout, amp=0.005):
+    """A smooth contravariant velocity on the moving wall (face wall-axis, high)."""
+    nodes = I.face_nodes(n, layout[0], 1)
+    r = I.grid(n)
+    p, s = r[layout[1]][nodes], r[layout[2]][nodes]
+    u = np.zeros((3, nodes.size))
+    u[layout[2]] = amp * np.cos(2 * np.pi * p / n[layout[1]]) * np.sin(np.pi * s / (n[layout[2]] - 1)) ** 2
+    return u
+
+
+@pytest.mark.parametrize("name,n,layout,kind", TILED, ids=[t[0] for t in TILED])
+def test_tiled_fp32_fast_path(name, n, layout, kind):
+    rng = np.random.default_rng(11)
+    if kind == "periodic":
+        w = I.periodic_channel(n, 0.7, 0.04, 3, 0.05, 12, layout=layout)
+        w["faces"] = {(layout[0], 1): smooth_wall_velocity(n, layout)}
+    else:
+        dfm = I.fourier_deformation(n, 4, 0.06, seed=13, flow_periodic=False, kmax=2, lmax=1, layout=layout)
+        ch = I.channel_chart(n, dfm, layout)
+        lo, hi = [P] * 3, [P] * 3
+        lo[layout[0]] = hi[layout[0]] = W
+        lo[layout[2]], hi[layout[2]] = IN, OUT
+        w = dict(n=n, bc_lo=tuple(lo), bc_hi=tuple(hi), tau=0.65, fext=(0.0, 0.0, 0.0), chart=ch,
+                 faces={(layout[2], 0): I.inflow_profile(n, ch, 0.04, layout),
+                        (layout[0], 1): smooth_wall_velocity(n, layout)})
+    g, o = make_pair(w, "fp32")
+    N = int(np.prod(n))
+    rho0 = 1 + 0.005 * rng.standard_normal(N)
+    u0 = 0.01 * rng.standard_normal((3, N))
+    g.init_equilibrium(rho0, u0)
+    o.init(rho0, u0)
+    g.step(120)
+    o.step(120)
+    assert g.check()
+    compare(g, o, w["chart"].J9, TOL["fp32"], name)
