@@ -284,7 +284,7 @@ def main():
                    "state_finite_after_run": ok},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "k_step_fused (one launch per LBM step)", "bytes_per_node": bpn,
+                     "kernel": "one LBM step: k_momentum_flat + k_step_flat", "bytes_per_node": bpn,
                      "step_ms": step_ms},
         "e2e": e2e,
         "gpu_launches": launches,

@@ -3,7 +3,6 @@
 // kernels themselves live in kernels.cuh (one instantiation per format).
 #include <cstdint>
 #include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -145,41 +144,6 @@ cslbm_status stage_in(cslbm_ctx* c, const double* src, int ncomp, long long v0, 
     return CSLBM_OK;
 }
 
-// Tensor maps of the geometry [25][N] and history [10][N] buffers viewed as
-// 4-D (x, y, z, component) arrays with a 32 x 8 x 1 x all-components box,
-// for the bulk-copy step.  Returns false when they cannot be made (the
-// general step kernel is used then).
-bool make_tensor_maps(cslbm_ctx* c)
-{
-    if (c->p.storage != CSLBM_FP32 || c->n[0] % 32 || c->n[1] % 8) return false;
-    typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn ||
-        q != cudaDriverEntryPointSuccess)
-        return false;
-    encode_fn encode = (encode_fn)fn;
-    const cuuint64_t n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
-    for (int k = 0; k < 2; k++) {
-        for (int which = 0; which < 2; which++) {
-            const cuuint64_t comps = which ? 10 : 25;
-            const cuuint64_t dims[4] = {n0, n1, n2, comps};
-            const cuuint64_t strides[3] = {n0 * 4, n0 * n1 * 4, n0 * n1 * n2 * 4};
-            const cuuint32_t box[4] = {32, 8, 1, (cuuint32_t)comps};
-            const cuuint32_t estr[4] = {1, 1, 1, 1};
-            CUtensorMap* m = which ? &c->tm_hist[k] : &c->tm_geo[k];
-            void* base = which ? c->H[k] : c->G[k];
-            if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return false;
-        }
-    }
-    return true;
-}
-
 cslbm_status read_scratch(cslbm_ctx* c, double* out, int k)
 {
     CUDA_TRY(cudaMemcpyAsync(out, c->scratch, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -271,8 +235,6 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
     c->pc = c->hc = c->gc = 0;
     c->has_state = 0;
     c->ops = ops_for(p->storage);
-    c->use_tma = make_tensor_maps(c) ? 1 : 0;
-    { const char* e = getenv("CSLBM_STEP"); c->step_kind = e ? atoi(e) : 0; }
     cslbm_status s = CSLBM_OK;
     if (cudaMemsetAsync(ws, 0, L.total, c->stream) != cudaSuccess) s = fail(CSLBM_ECUDA, "workspace memset failed");
     if (!s) s = set_flat(c, 0);
@@ -405,7 +367,7 @@ cslbm_status cslbm_step(cslbm_ctx* c, int nsteps)
             CUDA_TRY(cudaEventRecord(e[0], c->stream));
         }
         c->ops->step(c, 0);
-        c->launches += c->step_kind == 1 ? 2 : 1;
+        c->launches += 2;  // momentum pass + step pass
         LAUNCH_CHECK("step kernel");
         if (c->prof) {
             CUDA_TRY(cudaEventRecord(c->ev.back(), c->stream));
@@ -478,9 +440,6 @@ cslbm_status cslbm_check(cslbm_ctx* c)
     LAUNCH_CHECK("check kernel");
     double bad = 0.0;
     if (cslbm_status s = read_scratch(c, &bad, 1)) return s;
-    int tmo = 0;
-    CUDA_TRY(cudaMemcpy(&tmo, c->scratch + 40, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tmo) return fail(CSLBM_ETIMEOUT, "a bounded wait of the step kernel ran out (copy engine stalled)");
     if (bad > 0.0) {
         char m[96];
         snprintf(m, sizeof m, "%.0f nodes with non-finite density or |v| > 0.3", bad);

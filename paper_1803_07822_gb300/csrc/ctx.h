@@ -2,7 +2,6 @@
 // per-storage-format kernel units.  Not part of the public interface.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -35,12 +34,6 @@ struct cslbm_ctx {
     int has_state;
     int metric_check_pending;  // a metric kernel ran without a host check
     const cslbm_ops* ops;
-    // tensor maps of the geometry and history buffers for the bulk-copy step
-    // (FP32 storage, n0 % 32 == 0, n1 % 8 == 0)
-    int use_tma;
-    int step_kind;  // experiment: 0 fused, 1 flat, 2 staged
-    CUtensorMap tm_geo[2];
-    CUtensorMap tm_hist[2];
     // profiling
     int prof;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of profiled steps
@@ -60,8 +53,8 @@ struct cslbm_ops {
                          long long v0, long long cnt);
     // jf <- rho u of the current state
     void (*momentum_field)(const cslbm_ctx*);
-    // one fused step P[pc],H[hc] -> P[1-pc],H[1-hc]; force_only: only H[1-hc]
-    // from the momentum field jf (initialisation)
+    // one time step P[pc],H[hc] -> P[1-pc],H[1-hc] (momentum pass + step
+    // pass); force_only: only H[1-hc] from the momentum field jf
     void (*step)(const cslbm_ctx*, int force_only);
     // P[pc] slots -= F/2 of H[hc] (end of initialisation)
     void (*half_shift)(const cslbm_ctx*);

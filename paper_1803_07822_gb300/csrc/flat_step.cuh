@@ -65,16 +65,17 @@ __device__ __noinline__ void momentum_boundary(const Lat& L, const S* __restrict
     jf[v] = j;
 }
 
+// launch shape of both passes: 32 x 8 node tiles, one grid row per plane
+constexpr int BXN = 32, BYN = 8;
+
 template <class S, class R>
-__global__ void __launch_bounds__(256) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                       const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
+__global__ void __launch_bounds__(BXN * BYN) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                             const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
 {
     const unsigned N = (unsigned)L.N;
-    const unsigned v = blockIdx.x * 256u + threadIdx.x;
-    if (v >= N) return;
-    const int x = (int)(v % (unsigned)L.n[0]);
-    const unsigned r = v / (unsigned)L.n[0];
-    const int y = (int)(r % (unsigned)L.n[1]), z = (int)(r / (unsigned)L.n[1]);
+    const int x = blockIdx.x * BXN + threadIdx.x, y = blockIdx.y * BYN + threadIdx.y, z = blockIdx.z;
+    if (x >= L.n[0] || y >= L.n[1]) return;
+    const unsigned v = ((unsigned)z * L.n[1] + y) * (unsigned)L.n[0] + x;
     if (on_boundary(L, x, y, z)) {
         momentum_boundary<S, R>(L, P, hist, geo, x, y, z, jf);
         return;
@@ -205,16 +206,14 @@ __device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ P
 }
 
 template <class S, class R>
-__global__ void __launch_bounds__(256, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
-                                                      const R* __restrict__ hin, R* __restrict__ hout,
-                                                      const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+__global__ void __launch_bounds__(BXN * BYN, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                            const R* __restrict__ hin, R* __restrict__ hout,
+                                                            const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
 {
     const unsigned N = (unsigned)L.N;
-    const unsigned v = blockIdx.x * 256u + threadIdx.x;
-    if (v >= N) return;
-    const int x = (int)(v % (unsigned)L.n[0]);
-    const unsigned r = v / (unsigned)L.n[0];
-    const int y = (int)(r % (unsigned)L.n[1]), z = (int)(r / (unsigned)L.n[1]);
+    const int x = blockIdx.x * BXN + threadIdx.x, y = blockIdx.y * BYN + threadIdx.y, z = blockIdx.z;
+    if (x >= L.n[0] || y >= L.n[1]) return;
+    const unsigned v = ((unsigned)z * L.n[1] + y) * (unsigned)L.n[0] + x;
     if (on_boundary(L, x, y, z)) {
         step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
         return;
@@ -240,13 +239,24 @@ __global__ void __launch_bounds__(256, 2) k_step_flat(Lat L, const S* __restrict
     step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
 }
 
+inline dim3 flat_grid(const cslbm_ctx* c)
+{
+    return dim3((c->n[0] + BXN - 1) / BXN, (c->n[1] + BYN - 1) / BYN, c->n[2]);
+}
+
+template <class S, class R>
+void launch_momentum(const cslbm_ctx* c, const Lat& L, const S* P, const R* hin, const R* geo)
+{
+    k_momentum_flat<S, R><<<flat_grid(c), dim3(BXN, BYN), 0, c->stream>>>(L, P, hin, geo, (Mom4<R>*)c->jf);
+}
+
+// one time step: momentum pass, then the step pass
 template <class S, class R>
 void launch_flat_step(const cslbm_ctx* c, const Lat& L, const S* Pin, S* Pout, const R* hin, R* hout, const R* geo)
 {
-    const unsigned nb = (unsigned)((c->N + 255) / 256);
-    Mom4<R>* jf = (Mom4<R>*)c->jf;
-    k_momentum_flat<S, R><<<nb, 256, 0, c->stream>>>(L, Pin, hin, geo, jf);
-    k_step_flat<S, R><<<nb, 256, 0, c->stream>>>(L, Pin, Pout, hin, hout, geo, jf);
+    launch_momentum<S, R>(c, L, Pin, hin, geo);
+    k_step_flat<S, R><<<flat_grid(c), dim3(BXN, BYN), 0, c->stream>>>(L, Pin, Pout, hin, hout, geo,
+                                                                         (const Mom4<R>*)c->jf);
 }
 
 }  // namespace cslbm

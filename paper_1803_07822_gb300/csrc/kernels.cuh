@@ -5,16 +5,9 @@
 
 #include "ctx.h"
 #include "flat_step.cuh"
-#include "fused_step.cuh"
 #include "lbm_device.cuh"
 
 namespace cslbm {
-
-// bulk-copy step for FP32 storage on tile-aligned lattices (fused_tma.cuh)
-struct Lat;
-bool tma_eligible(const cslbm_ctx* c);
-void launch_tma_step(const cslbm_ctx* c, const Lat& L, const float* Pin, float* Pout, const float* hin, float* hout,
-                     const float* geo);
 
 constexpr int TPB = 256;
 
@@ -182,7 +175,7 @@ __device__ __forceinline__ void node_moments(const Lat& L, const S* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Pieces of the step shared by the fused step kernel and the initial forcing.
+// Pieces of the step used by the initial forcing pass.
 // ---------------------------------------------------------------------------
 // T = Pi^eq + (1 - 1/2tau)(Pi - Pi^eq), Pi^eq = rho theta g^-1 + j j / rho,
 // Pi = sqrt(g)(c_s^2 delta + m2) + C'/2    (Eq. fields3, App. B)
@@ -560,8 +553,7 @@ template <class S, class R> struct Launch {
     }
     static void momentum_field(const cslbm_ctx* c)
     {
-        k_momentum_flat<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
-                                                                    (Mom4<R>*)c->jf);
+        launch_momentum<S, R>(c, make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc));
     }
     static void step(const cslbm_ctx* c, int force_only)
     {
@@ -571,17 +563,7 @@ template <class S, class R> struct Launch {
                                                                  G(c, c->gc), c->jf);
             return;
         }
-        if (c->step_kind == 1) {
-            launch_flat_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
-            return;
-        }
-        if constexpr (sizeof(S) == 4 && sizeof(R) == 4) {
-            if (c->step_kind == 2 && tma_eligible(c)) {
-                launch_tma_step(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
-                return;
-            }
-        }
-        launch_fused_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
+        launch_flat_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
     }
     static void half_shift(const cslbm_ctx* c)
     {
