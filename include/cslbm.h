@@ -158,6 +158,23 @@ cslbm_status cslbm_profile_enable(cslbm_ctx* ctx, int enable);
  * Synchronises the stream. */
 cslbm_status cslbm_profile_read(cslbm_ctx* ctx, double* step_ms, long long* nsteps, long long* launches);
 
+/* Total mass as cslbm_total_mass, for callers that may not allocate device
+ * memory and must leave the context's reduction scratch alone: code in a
+ * real-time loop or a host callback that must not enter the CUDA allocator,
+ * or a plugin whose host framework owns every allocation.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ * Allocates nothing: the per-block partial sums live in a file-scope device
+ * array of 2^18 doubles (2 MiB, held by every GPU that loads the library
+ * until the process exits), so lattices of more than 67,108,864 nodes are
+ * rejected with CSLBM_EINVAL.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with the context's device
+ * current, which must be the current device; make that first call before any
+ * stream capture.  The partials are added in a fixed order, so repeated calls
+ * on the same state give the same bits.  Every call shares the array and it
+ * keeps the last call's contents: calls that overlap on the GPU race.  Syncs
+ * the context's stream. */
+cslbm_status cslbm_total_mass_static(cslbm_ctx* ctx, double* out);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* cslbm_last_error(void);
 

@@ -48,6 +48,7 @@ SIGNATURES = {
     "cslbm_step": [_P, _I],
     "cslbm_get_moments": [_P, _P, _P, _I, _I],
     "cslbm_total_mass": [_P, _D],
+    "cslbm_total_mass_static": [_P, _D],
     "cslbm_wall_force": [_P, _I, _I, _D],
     "cslbm_check": [_P],
     "cslbm_state_bytes": [_P, ctypes.POINTER(_SZ)],

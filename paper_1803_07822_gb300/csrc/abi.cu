@@ -189,6 +189,8 @@ cslbm_status run_metric(cslbm_ctx* c, const double* g6, const double* dg18, int 
 
 }  // namespace
 
+cslbm_status cslbm_record_error(cslbm_status s, const char* msg) { return fail(s, msg); }
+
 extern "C" {
 
 cslbm_status cslbm_workspace_bytes(const cslbm_params* p, size_t* bytes)

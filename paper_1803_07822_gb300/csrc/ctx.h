@@ -72,6 +72,9 @@ struct cslbm_ops {
     void (*check)(const cslbm_ctx*, double* acc);
 };
 
+// records the message cslbm_last_error() returns on this thread; returns s
+cslbm_status cslbm_record_error(cslbm_status s, const char* msg);
+
 extern const cslbm_ops cslbm_ops_fp32;
 extern const cslbm_ops cslbm_ops_fp16;
 extern const cslbm_ops cslbm_ops_bf16;

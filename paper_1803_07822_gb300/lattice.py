@@ -132,6 +132,13 @@ class CurvedLattice:
         call("cslbm_total_mass", self.ctx, ctypes.byref(out))
         return out.value
 
+    def total_mass_static(self):
+        """Total mass without touching the workspace scratch or allocating
+        (per-block partials in a fixed device array; see cslbm.h)."""
+        out = ctypes.c_double(0.0)
+        call("cslbm_total_mass_static", self.ctx, ctypes.byref(out))
+        return out.value
+
     def wall_force(self, axis, side):
         out = (ctypes.c_double * 3)()
         call("cslbm_wall_force", self.ctx, axis, side, out)

@@ -1,0 +1,49 @@
+"""The allocation-free total-mass entry point (cslbm_total_mass_static).
+
+It serves callers that may not allocate device memory where they need the
+mass (a real-time loop or host callback that must stay out of the CUDA
+allocator, a plugin whose framework owns all allocations).  Its partial sums
+live in a fixed device array instead of the context's workspace.  Checked
+through the C ABI against cslbm_total_mass on two calls in a row, on two
+lattices, so that the second call runs on the array the first one left.
+This file is collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1803_07822_gb300 import _abi
+from paper_1803_07822_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def mass_pair(lat):
+    lib = _abi.load()
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    assert lib.cslbm_total_mass(lat.ctx, ctypes.byref(a)) == _abi.OK, lib.cslbm_last_error()
+    assert lib.cslbm_total_mass_static(lat.ctx, ctypes.byref(b)) == _abi.OK, lib.cslbm_last_error()
+    return a.value, b.value
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_static_mass_matches_workspace_mass_twice(storage):
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+    w1 = I.plain_fp64_channel()
+    w2 = I.dynamic_channel(n=(37, 41, 23), seed=7, n_modes=4, amp=0.05, tau=0.7, re=10.0, kmax=2, lmax=1)
+    results = []
+    for w in (w1, w2):
+        lat = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=storage)
+        lat.set_chart(w["chart"])
+        for (a, s), u in w["faces"].items():
+            lat.set_boundary_velocity(a, s, u)
+        lat.init_equilibrium()
+        lat.step(25)
+        ref, got = mass_pair(lat)
+        again = lat.total_mass_static()
+        assert got == again  # fixed summation order: the same bits on a repeat
+        results.append((ref, got))
+    for ref, got in results:
+        assert abs(got - ref) <= 1e-12 * abs(ref)
+    assert results[0][0] != results[1][0]
