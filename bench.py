@@ -43,6 +43,12 @@ STEPS_PER_CYCLE = 10
 # coefficients read + written (FP32), 25 geometry values read (FP32)
 BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 + 80 + 100,
                   "bf16": 19 * 2 * 2 + 80 + 100, "fp64": 19 * 8 * 2 + 80 + 100}
+# DRAM bytes per node update (dram__bytes_read.sum + dram__bytes_write.sum of
+# k_momentum_flat + k_step_flat) from one ncu capture of the 64x128x64 crop of
+# the same channel, FP32 storage; both passes touch every node once, so the
+# per-launch traffic scales with the node count.  Only valid for the kernels
+# as they were captured.
+MEASURED_DRAM_BYTES_PER_NODE = {"fp32": (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
 
 
 def workload_spec(name):
@@ -274,6 +280,8 @@ def main():
     step_ms = step_ms_total / max(nprof, 1)
     bpn = BYTES_PER_NODE[spec["storage"]]
     achieved = bpn * N / (step_ms * 1e-3) / 1e9
+    mb = MEASURED_DRAM_BYTES_PER_NODE.get(spec["storage"])
+    traffic = None if mb is None else mb * N
     e2e = None if args.no_e2e else end_to_end(args, lat, snaps, N, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -283,7 +291,7 @@ def main():
                    "l2": "inputs > L2 (1.4 GB of state per LBM step), no flush",
                    "state_finite_after_run": ok},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "one LBM step: k_momentum_flat + k_step_flat", "bytes_per_node": bpn,
                      "step_ms": step_ms},
         "e2e": e2e,

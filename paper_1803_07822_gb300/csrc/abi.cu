@@ -68,6 +68,7 @@ cslbm_status validate(const cslbm_params* p)
     }
     if (!(p->tau > 0.5)) return fail(CSLBM_EINVAL, "tau must exceed 1/2");
     if (!ops_for(p->storage)) return fail(CSLBM_EINVAL, "unknown storage format");
+    if (p->n[2] > 65535) return fail(CSLBM_EINVAL, "n[2] must be at most 65535 (one launch row per plane)");
     // the step kernel indexes fields with 32-bit offsets (25 components of N)
     if (25LL * p->n[0] * p->n[1] * p->n[2] >= (1LL << 32))
         return fail(CSLBM_EINVAL, "lattice too large: at most 171,798,691 nodes per context");

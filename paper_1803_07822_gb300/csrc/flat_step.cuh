@@ -65,17 +65,30 @@ __device__ __noinline__ void momentum_boundary(const Lat& L, const S* __restrict
     jf[v] = j;
 }
 
-// launch shape of both passes: 32 x 8 node tiles, one grid row per plane
-constexpr int BXN = 32, BYN = 8;
+// launch shape of both passes: blocks of 256 consecutive nodes of a plane
+// (blockIdx.x), one grid row per plane (blockIdx.y)
+constexpr int TB = 256;
+
+__device__ __forceinline__ bool flat_node(const Lat& L, int& x, int& y, int& z, unsigned& v)
+{
+    const unsigned n01 = (unsigned)L.n[0] * L.n[1];
+    const unsigned r = blockIdx.x * (unsigned)TB + threadIdx.x;
+    if (r >= n01) return false;
+    y = (int)(r / (unsigned)L.n[0]);
+    x = (int)(r - (unsigned)y * L.n[0]);
+    z = blockIdx.y;
+    v = (unsigned)z * n01 + r;
+    return true;
+}
 
 template <class S, class R>
-__global__ void __launch_bounds__(BXN * BYN) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                             const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
+__global__ void __launch_bounds__(TB) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                      const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
 {
     const unsigned N = (unsigned)L.N;
-    const int x = blockIdx.x * BXN + threadIdx.x, y = blockIdx.y * BYN + threadIdx.y, z = blockIdx.z;
-    if (x >= L.n[0] || y >= L.n[1]) return;
-    const unsigned v = ((unsigned)z * L.n[1] + y) * (unsigned)L.n[0] + x;
+    int x, y, z;
+    unsigned v;
+    if (!flat_node(L, x, y, z, v)) return;
     if (on_boundary(L, x, y, z)) {
         momentum_boundary<S, R>(L, P, hist, geo, x, y, z, jf);
         return;
@@ -206,14 +219,14 @@ __device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ P
 }
 
 template <class S, class R>
-__global__ void __launch_bounds__(BXN * BYN, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
-                                                            const R* __restrict__ hin, R* __restrict__ hout,
-                                                            const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+__global__ void __launch_bounds__(TB, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                     const R* __restrict__ hin, R* __restrict__ hout,
+                                                     const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
 {
     const unsigned N = (unsigned)L.N;
-    const int x = blockIdx.x * BXN + threadIdx.x, y = blockIdx.y * BYN + threadIdx.y, z = blockIdx.z;
-    if (x >= L.n[0] || y >= L.n[1]) return;
-    const unsigned v = ((unsigned)z * L.n[1] + y) * (unsigned)L.n[0] + x;
+    int x, y, z;
+    unsigned v;
+    if (!flat_node(L, x, y, z, v)) return;
     if (on_boundary(L, x, y, z)) {
         step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
         return;
@@ -241,13 +254,13 @@ __global__ void __launch_bounds__(BXN * BYN, 2) k_step_flat(Lat L, const S* __re
 
 inline dim3 flat_grid(const cslbm_ctx* c)
 {
-    return dim3((c->n[0] + BXN - 1) / BXN, (c->n[1] + BYN - 1) / BYN, c->n[2]);
+    return dim3((unsigned)(((long long)c->n[0] * c->n[1] + TB - 1) / TB), c->n[2]);
 }
 
 template <class S, class R>
 void launch_momentum(const cslbm_ctx* c, const Lat& L, const S* P, const R* hin, const R* geo)
 {
-    k_momentum_flat<S, R><<<flat_grid(c), dim3(BXN, BYN), 0, c->stream>>>(L, P, hin, geo, (Mom4<R>*)c->jf);
+    k_momentum_flat<S, R><<<flat_grid(c), TB, 0, c->stream>>>(L, P, hin, geo, (Mom4<R>*)c->jf);
 }
 
 // one time step: momentum pass, then the step pass
@@ -255,7 +268,7 @@ template <class S, class R>
 void launch_flat_step(const cslbm_ctx* c, const Lat& L, const S* Pin, S* Pout, const R* hin, R* hout, const R* geo)
 {
     launch_momentum<S, R>(c, L, Pin, hin, geo);
-    k_step_flat<S, R><<<flat_grid(c), dim3(BXN, BYN), 0, c->stream>>>(L, Pin, Pout, hin, hout, geo,
+    k_step_flat<S, R><<<flat_grid(c), TB, 0, c->stream>>>(L, Pin, Pout, hin, hout, geo,
                                                                          (const Mom4<R>*)c->jf);
 }
 
