@@ -51,6 +51,13 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
 MEASURED_DRAM_BYTES_PER_NODE = {"fp32": (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
 
 
+def row_staged(n, storage, step_kernel):
+    """Whether the library takes the row-staged step pass for this lattice
+    (the rule include/cslbm.h states for CSLBM_STEP_AUTO)."""
+    sb = {"fp32": 4, "fp16": 2, "bf16": 2}.get(storage)
+    return step_kernel == "auto" and sb is not None and n[0] <= 256 and n[0] % 4 == 0 and (n[0] * sb) % 16 == 0
+
+
 def workload_spec(name):
     if name == "dynamic":
         return dict(n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
@@ -212,6 +219,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--snapshots", type=int, default=3)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "flat"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -229,7 +237,8 @@ def main():
     N = int(np.prod(spec["n"]))
     times = [500.0 + STEPS_PER_CYCLE * k for k in range(args.snapshots + 1)]
     snaps = snapshots(w, times)
-    lat = CurvedLattice(spec["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=spec["storage"])
+    lat = CurvedLattice(spec["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=spec["storage"],
+                        step_kernel=args.step_kernel)
     # device-resident inputs for the kernel-throughput run
     dev = []
     for ch, faces in snaps:
@@ -280,7 +289,8 @@ def main():
     step_ms = step_ms_total / max(nprof, 1)
     bpn = BYTES_PER_NODE[spec["storage"]]
     achieved = bpn * N / (step_ms * 1e-3) / 1e9
-    mb = MEASURED_DRAM_BYTES_PER_NODE.get(spec["storage"])
+    rows = row_staged(spec["n"], spec["storage"], args.step_kernel)
+    mb = None if rows else MEASURED_DRAM_BYTES_PER_NODE.get(spec["storage"])
     traffic = None if mb is None else mb * N
     e2e = None if args.no_e2e else end_to_end(args, lat, snaps, N, world)
     line = {
@@ -292,7 +302,7 @@ def main():
                    "state_finite_after_run": ok},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "one LBM step: k_momentum_flat + k_step_flat", "bytes_per_node": bpn,
+                     "kernel": "one LBM step: k_momentum_flat + " + ("k_step_rows" if rows else "k_step_flat"), "bytes_per_node": bpn,
                      "step_ms": step_ms},
         "e2e": e2e,
         "gpu_launches": launches,

@@ -67,7 +67,14 @@ typedef struct {
     double fext[3];     /* body-force density, contravariant, constant (Eq. forcing-B) */
     int storage;        /* cslbm_storage */
     int transform_flags;/* bit 0: transform a_(2) itself instead of the momentum flux Pi */
+    int step_kernel;    /* cslbm_step_kernel: which step pass runs (same results up to rounding) */
 } cslbm_params;
+
+/* Step pass.  AUTO takes the row-staged pass (whole lattice rows copied to
+ * shared memory by the bulk-copy engine) where it applies -- FP32/FP16/BF16
+ * storage, n[0] <= 256 and n[0] * bytes per stored population a multiple of
+ * 16 -- and the flat gather pass elsewhere; FLAT always takes the flat pass. */
+typedef enum { CSLBM_STEP_AUTO = 0, CSLBM_STEP_FLAT = 1 } cslbm_step_kernel;
 
 typedef struct cslbm_ctx cslbm_ctx;
 

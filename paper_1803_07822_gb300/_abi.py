@@ -13,6 +13,7 @@ from . import buildlib as _build
 
 OK, EINVAL, ECUDA, ENOMEM, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 FP32, FP16S, BF16S, FP64 = range(4)
+STEP_AUTO, STEP_FLAT = range(2)
 PERIODIC, WALL, INFLOW, OUTFLOW = range(4)
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}
@@ -27,7 +28,8 @@ class CslbmError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double), ("fext", ctypes.c_double * 3),
-                ("storage", ctypes.c_int), ("transform_flags", ctypes.c_int)]
+                ("storage", ctypes.c_int), ("transform_flags", ctypes.c_int),
+                ("step_kernel", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -68,6 +68,8 @@ cslbm_status validate(const cslbm_params* p)
     }
     if (!(p->tau > 0.5)) return fail(CSLBM_EINVAL, "tau must exceed 1/2");
     if (!ops_for(p->storage)) return fail(CSLBM_EINVAL, "unknown storage format");
+    if (p->step_kernel != CSLBM_STEP_AUTO && p->step_kernel != CSLBM_STEP_FLAT)
+        return fail(CSLBM_EINVAL, "unknown step kernel");
     if (p->n[2] > 65535) return fail(CSLBM_EINVAL, "n[2] must be at most 65535 (one launch row per plane)");
     // the step kernel indexes fields with 32-bit offsets (25 components of N)
     if (25LL * p->n[0] * p->n[1] * p->n[2] >= (1LL << 32))
@@ -192,6 +194,78 @@ cslbm_status run_metric(cslbm_ctx* c, const double* g6, const double* dg18, int 
 
 cslbm_status cslbm_record_error(cslbm_status s, const char* msg) { return fail(s, msg); }
 
+namespace {
+
+// The row-staged step pass: plan, tensor maps and side stream, when the
+// storage, shape and device allow it (otherwise the flat pass serves).
+void rows_prepare(cslbm_ctx* c)
+{
+    cslbm_rows& R = c->rows;
+    R.ok = 0;
+    if (c->p.step_kernel != CSLBM_STEP_AUTO || c->p.storage == CSLBM_FP64) return;
+    int max_smem = 0;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return;
+    if (!cslbm::rows::make_plan(c->n, c->p.bc_lo[2] == CSLBM_PERIODIC, (int)c->s_bytes, max_smem, R.plan)) return;
+    typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn ||
+        q != cudaDriverEntryPointSuccess)
+        return;
+    encode_fn encode = (encode_fn)fn;
+    const cuuint64_t n0 = c->n[0], n1 = c->n[1], n2 = c->n[2], N = c->N, sb = c->s_bytes;
+    const cuuint32_t TR = R.plan.TR, NT = cslbm::rows::NT;
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    auto mk = [&](CUtensorMap* m, CUtensorMapDataType t, cuuint32_t rank, void* base, const cuuint64_t* dims,
+                  const cuuint64_t* strides, const cuuint32_t* box) {
+        return encode(m, t, rank, base, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    const CUtensorMapDataType tpop = sb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; k++) {
+        const cuuint64_t pd[4] = {n0, n1, n2, 19}, ps[3] = {n0 * sb, n0 * n1 * sb, N * sb};
+        const cuuint32_t pb[4] = {(cuuint32_t)n0, TR, 1, 1};
+        ok = ok && mk(&R.pop[k], tpop, 4, c->P[k], pd, ps, pb);
+        const cuuint64_t gd[2] = {N, 25}, gs[1] = {N * 4};
+        const cuuint32_t gb[2] = {NT, 25};
+        ok = ok && mk(&R.geo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->G[k], gd, gs, gb);
+        const cuuint64_t hd[2] = {N, 10};
+        const cuuint32_t hb[2] = {NT, 10};
+        ok = ok && mk(&R.hist[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->H[k], hd, gs, hb);
+    }
+    const cuuint64_t jd[4] = {4, n0, n1, n2}, js[3] = {16, 16 * n0, 16 * n0 * n1};
+    const cuuint32_t jb[4] = {4, (cuuint32_t)n0, TR + 2, 1};
+    ok = ok && mk(&R.jf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->jf, jd, js, jb);
+    if (!ok) return;
+    if (cudaStreamCreateWithFlags(&R.side, cudaStreamNonBlocking) != cudaSuccess) return;
+    if (cudaEventCreateWithFlags(&R.fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(R.side);
+        return;
+    }
+    if (cudaEventCreateWithFlags(&R.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(R.fork);
+        cudaStreamDestroy(R.side);
+        return;
+    }
+    R.ok = 1;
+}
+
+void rows_release(cslbm_ctx* c)
+{
+    if (!c->rows.ok) return;
+    cudaStreamSynchronize(c->rows.side);
+    cudaEventDestroy(c->rows.fork);
+    cudaEventDestroy(c->rows.join);
+    cudaStreamDestroy(c->rows.side);
+    c->rows.ok = 0;
+}
+
+}  // namespace
+
 extern "C" {
 
 cslbm_status cslbm_workspace_bytes(const cslbm_params* p, size_t* bytes)
@@ -216,6 +290,7 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
     c->theta = p->theta > 0 ? p->theta : 1.0 / 3.0;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     c->s_bytes = L.s_bytes;
     c->r_bytes = L.r_bytes;
     char* b = (char*)ws;
@@ -252,6 +327,8 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
         delete c;
         return s;
     }
+    rows_prepare(c);
+    cudaGetLastError();  // a pass that could not be prepared leaves no error behind
     *out = c;
     return CSLBM_OK;
 }
@@ -261,6 +338,7 @@ cslbm_status cslbm_destroy(cslbm_ctx* c)
     if (!c) return fail(CSLBM_EINVAL, "ctx is null");
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    rows_release(c);
     delete c;
     return CSLBM_OK;
 }
@@ -369,8 +447,7 @@ cslbm_status cslbm_step(cslbm_ctx* c, int nsteps)
             c->ev.push_back(e[1]);
             CUDA_TRY(cudaEventRecord(e[0], c->stream));
         }
-        c->ops->step(c, 0);
-        c->launches += 2;  // momentum pass + step pass
+        c->launches += c->ops->step(c, 0);
         LAUNCH_CHECK("step kernel");
         if (c->prof) {
             CUDA_TRY(cudaEventRecord(c->ev.back(), c->stream));
@@ -437,6 +514,17 @@ cslbm_status cslbm_check(cslbm_ctx* c)
     if (!c->has_state) return fail(CSLBM_ESTATE, "no state");
     if (c->metric_check_pending)
         if (cslbm_status s = metric_flag(c)) return s;
+    {
+        int terr = 0;
+        CUDA_TRY(cudaMemcpyAsync(&terr, step_error_flag(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (terr) {
+            CUDA_TRY(cudaMemsetAsync(step_error_flag(c), 0, sizeof(int), c->stream));
+            char m[96];
+            snprintf(m, sizeof m, "a bounded wait of the row-staged step pass ran out (code %d)", terr);
+            return fail(CSLBM_ETIMEOUT, m);
+        }
+    }
     CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 8 * sizeof(double), c->stream));
     c->ops->check(c, c->scratch);
     c->launches++;

@@ -2,14 +2,31 @@
 // per-storage-format kernel units.  Not part of the public interface.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 #include <vector>
 
 #include "../../include/cslbm.h"
+#include "rows_plan.h"
 
 struct cslbm_ops;
+
+// Resources of the row-staged step pass, made at creation when it applies:
+// its plan, tensor maps of the buffers it stages (populations and history
+// per ping-pong buffer), and a side stream on which the face nodes are
+// stepped while the row pass runs.
+struct cslbm_rows {
+    int ok;
+    cslbm::rows::Plan plan;
+    CUtensorMap pop[2];   // [19][n2][n1][n0] populations, box n0 x TR
+    CUtensorMap jf;       // [n2][n1][n0][4] rho u, box 4 x n0 x (TR + 2)
+    CUtensorMap geo[2];   // [25][N] geometry, box NT x 25
+    CUtensorMap hist[2];  // [10][N] history, box NT x 10
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
 
 struct cslbm_ctx {
     cslbm_params p;
@@ -18,6 +35,7 @@ struct cslbm_ctx {
     double theta;
     cudaStream_t stream;
     int device;
+    int n_sm;        // multiprocessors of the device
     size_t s_bytes;  // bytes of one stored population
     size_t r_bytes;  // bytes of one compute-precision value
     void* P[2];      // [19][N] stored populations (pull layout, weight shifted)
@@ -35,6 +53,7 @@ struct cslbm_ctx {
     int metric_check_pending;  // a metric kernel ran without a host check
     const cslbm_ops* ops;
     // profiling
+    cslbm_rows rows;
     int prof;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of profiled steps
     long long prof_steps;
@@ -54,8 +73,9 @@ struct cslbm_ops {
     // jf <- rho u of the current state
     void (*momentum_field)(const cslbm_ctx*);
     // one time step P[pc],H[hc] -> P[1-pc],H[1-hc] (momentum pass + step
-    // pass); force_only: only H[1-hc] from the momentum field jf
-    void (*step)(const cslbm_ctx*, int force_only);
+    // pass); force_only: only H[1-hc] from the momentum field jf.  Returns
+    // the number of kernels it launched.
+    int (*step)(const cslbm_ctx*, int force_only);
     // P[pc] slots -= F/2 of H[hc] (end of initialisation)
     void (*half_shift)(const cslbm_ctx*);
     // chart change for nodes [v0, v0+cnt): P[pc],H[hc],G[gc] -> P[1-pc],H[1-hc] with G[1-gc]
@@ -71,6 +91,10 @@ struct cslbm_ops {
     // acc[0] += number of unstable nodes
     void (*check)(const cslbm_ctx*, double* acc);
 };
+
+// flag the row-staged step pass sets when one of its bounded waits runs out
+// (an int in the reduction scratch, zero from creation; cslbm_check reads it)
+inline int* step_error_flag(const cslbm_ctx* c) { return (int*)(c->scratch + 40); }
 
 // records the message cslbm_last_error() returns on this thread; returns s
 cslbm_status cslbm_record_error(cslbm_status s, const char* msg);

@@ -252,6 +252,76 @@ __global__ void __launch_bounds__(TB, 2) k_step_flat(Lat L, const S* __restrict_
     step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
 }
 
+// The nodes on non-periodic faces as up to six boxes without overlap: the
+// faces of axis 2 whole, those of axis 1 without the axis-2 face nodes, those
+// of axis 0 without the face nodes of axes 1 and 2.
+struct FaceList {
+    int nseg;
+    int lo[6][3], len[6][3];
+    long long start[7];
+};
+
+inline FaceList face_list(const cslbm_ctx* c)
+{
+    FaceList f{};
+    long long total = 0;
+    bool done[3] = {false, false, false};
+    for (int a = 2; a >= 0; a--) {
+        if (c->p.bc_lo[a] == CSLBM_PERIODIC) continue;
+        for (int side = 0; side < 2; side++) {
+            const int k = f.nseg++;
+            for (int b = 0; b < 3; b++) {
+                if (b == a) {
+                    f.lo[k][b] = side ? c->n[b] - 1 : 0;
+                    f.len[k][b] = 1;
+                } else if (done[b]) {
+                    f.lo[k][b] = 1;
+                    f.len[k][b] = c->n[b] - 2;
+                } else {
+                    f.lo[k][b] = 0;
+                    f.len[k][b] = c->n[b];
+                }
+            }
+            f.start[k] = total;
+            total += (long long)f.len[k][0] * f.len[k][1] * f.len[k][2];
+        }
+        done[a] = true;
+    }
+    f.start[f.nseg] = total;
+    return f;
+}
+
+// one step of the face nodes only (the interior comes from the row-staged pass)
+template <class S, class R>
+__global__ void __launch_bounds__(128) k_step_faces(const __grid_constant__ Lat L, const __grid_constant__ FaceList f,
+                                                    const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                    const R* __restrict__ hin, R* __restrict__ hout,
+                                                    const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+{
+    const long long i = blockIdx.x * 128LL + threadIdx.x;
+    if (i >= f.start[f.nseg]) return;
+    int k = 0;
+    while (k + 1 < f.nseg && i >= f.start[k + 1]) k++;
+    const long long r = i - f.start[k];
+    const int x = f.lo[k][0] + (int)(r % f.len[k][0]);
+    const long long q = r / f.len[k][0];
+    const int y = f.lo[k][1] + (int)(q % f.len[k][1]);
+    const int z = f.lo[k][2] + (int)(q / f.len[k][1]);
+    step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
+}
+
+template <class S, class R>
+int launch_faces(const cslbm_ctx* c, const Lat& L, const S* Pin, S* Pout, const R* hin, R* hout, const R* geo,
+                 cudaStream_t stream)
+{
+    const FaceList f = face_list(c);
+    const long long total = f.start[f.nseg];
+    if (total == 0) return 0;
+    k_step_faces<S, R><<<(unsigned)((total + 127) / 128), 128, 0, stream>>>(L, f, Pin, Pout, hin, hout, geo,
+                                                                               (const Mom4<R>*)c->jf);
+    return 1;
+}
+
 inline dim3 flat_grid(const cslbm_ctx* c)
 {
     return dim3((unsigned)(((long long)c->n[0] * c->n[1] + TB - 1) / TB), c->n[2]);

@@ -5,6 +5,7 @@
 
 #include "ctx.h"
 #include "flat_step.cuh"
+#include "row_step.cuh"
 #include "lbm_device.cuh"
 
 namespace cslbm {
@@ -555,15 +556,19 @@ template <class S, class R> struct Launch {
     {
         launch_momentum<S, R>(c, make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc));
     }
-    static void step(const cslbm_ctx* c, int force_only)
+    static int step(const cslbm_ctx* c, int force_only)
     {
         Lat L = make_lat(c);
         if (force_only) {
             k_forcing<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(L, P(c, c->pc), H(c, c->hc), H(c, 1 - c->hc),
                                                                  G(c, c->gc), c->jf);
-            return;
+            return 1;
+        }
+        if constexpr (!std::is_same<R, double>::value) {
+            if (c->rows.ok) return launch_rows_step<S>(c, L, c->pc, c->hc, c->gc, step_error_flag(c));
         }
         launch_flat_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));
+        return 2;
     }
     static void half_shift(const cslbm_ctx* c)
     {

@@ -1,0 +1,360 @@
+// LBM step pass with whole lattice rows staged in shared memory by the
+// bulk-copy engine (FP32 arithmetic; FP32, FP16 or BF16 storage).
+//
+// The step of a node reads, besides its own geometry (25 values) and forcing
+// history (10), the populations pulled from its neighbours (Eq. streaming)
+// and rho u at the 18 stencil sites of the lattice gradient (App. D).  When
+// every thread gathers these itself (k_step_flat), a node costs about a
+// hundred global loads with their address arithmetic, and too few of them
+// are in flight to cover the HBM latency.  Here a persistent CTA per SM
+// splits into NT/32 compute warps and one copy warp.  A tile is TR whole
+// x-rows of one plane (TR n0 <= NT nodes).  For a tile the copy warp issues
+// one bulk copy (cp.async.bulk, completion on the stage's mbarrier) per
+//   - population lambda and tile row: the source row (y - c_y, z - c_z) of
+//     array lambda.  It holds every value the row pulls in direction lambda,
+//     because the periodic wrap in x stays inside the row;
+//   - rho u row of the (TR + 2) x 3 rows around the tile (y0-1 .. y0+TR,
+//     z-1 .. z+1);
+//   - geometry and history component: TR n0 contiguous values;
+// into one of STAGES shared-memory stages.  The compute warps step the
+// tile of the previous stage from shared memory and store the new
+// populations and history straight to HBM.
+//
+// Nodes on a non-periodic face (boundary rule, ghost stencil) are left to
+// k_step_faces, a separate launch at full occupancy over the face nodes only;
+// their rows are not staged, and face planes get no tiles.  Every wait on an
+// mbarrier is bounded (half a second); one that runs out sets *err (the host
+// reports CSLBM_ETIMEOUT) and the CTA leaves after its copies have landed.
+#pragma once
+
+#include "flat_step.cuh"
+#include "rows_plan.h"
+
+namespace cslbm {
+namespace rows {
+
+constexpr unsigned long long kWaitNs = 500000000ull;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// false when the phase of the given parity did not complete within kWaitNs
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity)
+{
+    if (bar_try(b, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        if (bar_try(b, parity)) return true;
+        if (now_ns() - t0 > kWaitNs) return false;
+    }
+}
+// global -> shared bulk copy of `bytes` (16-byte aligned, a multiple of 16)
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* b)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(b))
+        : "memory");
+}
+
+// c^a of population l for a runtime l (bit masks instead of a table, which
+// would live in local memory)
+__device__ __forceinline__ int cvec_rt(int l, int a)
+{
+    constexpr unsigned plus[3] = {(1u << 1) | (1u << 7) | (1u << 9) | (1u << 11) | (1u << 13),
+                                  (1u << 3) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 17),
+                                  (1u << 5) | (1u << 11) | (1u << 14) | (1u << 15) | (1u << 18)};
+    constexpr unsigned minus[3] = {(1u << 2) | (1u << 8) | (1u << 10) | (1u << 12) | (1u << 14),
+                                   (1u << 4) | (1u << 8) | (1u << 9) | (1u << 16) | (1u << 18),
+                                   (1u << 6) | (1u << 12) | (1u << 13) | (1u << 16) | (1u << 17)};
+    const unsigned p = a == 0 ? plus[0] : (a == 1 ? plus[1] : plus[2]);
+    const unsigned m = a == 0 ? minus[0] : (a == 1 ? minus[1] : minus[2]);
+    return (int)((p >> l) & 1u) - (int)((m >> l) & 1u);
+}
+
+// tiled tensor copies (box of the map at the given element coordinates;
+// elements outside the tensor read as zero)
+__device__ __forceinline__ void tensor2(void* dst, const CUtensorMap* map, int c0, int c1, unsigned long long* b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(su32(b))
+        : "memory");
+}
+__device__ __forceinline__ void tensor4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                        unsigned long long* b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(b))
+        : "memory");
+}
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+__device__ __forceinline__ int wrap_or(int r, int n, bool periodic, bool& inside)
+{
+    if (r >= 0 && r < n) return r;
+    inside = periodic;
+    return r < 0 ? r + n : r - n;
+}
+
+// Tensor maps handed to the pass (grid constants).
+struct Maps {
+    CUtensorMap pop, jf, geo, hist;
+};
+
+// the copy warp: stage the rows of tile t into stage `st`, completing on bar.
+// Tiles away from the ends of a periodic y axis take one box per population,
+// per rho u layer, and for the geometry and the history (24 copies); the
+// first and last tile of a periodic y axis copy row by row, so that the rows
+// across the periodic seam come from the other end of the axis.
+template <class S>
+__device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const Maps& M, int t, unsigned char* st,
+                                           unsigned long long* bar, const S* __restrict__ Pin,
+                                           const Mom4<float>* __restrict__ jf, int lane)
+{
+    const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+    const unsigned N = (unsigned)L.N;
+    const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
+    const int TRe = min(pl.TR, n1 - y0);
+    const bool yper = L.bclo[1] == BC_PERIODIC, zper = L.bclo[2] == BC_PERIODIC;
+    const unsigned v0 = ((unsigned)z * n1 + y0) * n0;
+    const bool seam = yper && (y0 == 0 || y0 + pl.TR >= n1);
+    const int npop = seam ? Q * TRe : Q, njf = seam ? 3 * (TRe + 2) : 3;
+    const int total = npop + njf + 2;
+    for (int c = lane; c < total; c += 32) {
+        if (c < npop) {
+            const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0;
+            bool in = true;
+            const int zs = wrap_or(z - cvec_rt(l, 2), n2, zper, in);
+            if (!seam) {
+                const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
+                bar_expect_tx(bar, bytes);
+                tensor4(st + (size_t)l * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, l, bar);
+                continue;
+            }
+            const int y = y0 + r;
+            const int ys = wrap_or(y - cvec_rt(l, 1), n1, yper, in);
+            if (!in) continue;
+            const unsigned bytes = (unsigned)(n0 * sizeof(S));
+            bar_expect_tx(bar, bytes);
+            bulk_copy(st + (size_t)(l * NT + r * n0) * sizeof(S), Pin + (size_t)l * N + ((unsigned)zs * n1 + ys) * n0,
+                      bytes, bar);
+        } else if (c < npop + njf) {
+            const int k = c - npop, a = seam ? k / (TRe + 2) : k, b = seam ? k - a * (TRe + 2) : 0;
+            bool in = true;
+            const int zs = wrap_or(z - 1 + a, n2, zper, in);
+            if (!in) continue;
+            unsigned char* dst = st + pl.off_jf + (size_t)(a * pl.JS + b * n0) * sizeof(Mom4<float>);
+            if (!seam) {
+                const unsigned bytes = (unsigned)((pl.TR + 2) * n0 * sizeof(Mom4<float>));
+                bar_expect_tx(bar, bytes);
+                tensor4(dst, &M.jf, 0, 0, y0 - 1, zs, bar);
+                continue;
+            }
+            const int ys = wrap_or(y0 - 1 + b, n1, yper, in);
+            if (!in) continue;
+            const unsigned bytes = (unsigned)(n0 * sizeof(Mom4<float>));
+            bar_expect_tx(bar, bytes);
+            bulk_copy(dst, jf + ((unsigned)zs * n1 + ys) * n0, bytes, bar);
+        } else if (c == npop + njf) {
+            bar_expect_tx(bar, NGEO * NT * 4u);
+            tensor2(st + pl.off_geo, &M.geo, (int)v0, 0, bar);
+        } else {
+            bar_expect_tx(bar, NHIST * NT * 4u);
+            tensor2(st + pl.off_hist, &M.hist, (int)v0, 0, bar);
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_step_rows(const __grid_constant__ Lat L, const __grid_constant__ Plan pl, const __grid_constant__ Maps M,
+                const S* __restrict__ Pin, S* __restrict__ Pout, float* __restrict__ hout,
+                const Mom4<float>* __restrict__ jf, int* err)
+{
+    extern __shared__ __align__(128) unsigned char smem_rows[];
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_rows + STAGES * pl.stage_bytes);
+    unsigned long long* empty = full + STAGES;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const int n0 = L.n[0], n1 = L.n[1];
+
+    if (tid >= NT) {
+        // copy warp
+        const int lane = tid - NT;
+        int i = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < pl.ntiles; t += gridDim.x, i++) {
+            const int s = i % STAGES;
+            if (i >= STAGES) {
+                ok = bar_wait(&empty[s], ((i / STAGES) - 1) & 1);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            }
+            issue_tile<S>(L, pl, M, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s], Pin, jf, lane);
+            __syncwarp();
+            if (lane == 0) bar_arrive(&full[s]);
+        }
+        if (!ok && lane == 0) atomicOr(err, 1);
+        // leave only when the copies of the last stages have landed
+        for (int j = max(0, i - STAGES); j < i; j++)
+            if (!bar_wait(&full[j % STAGES], (j / STAGES) & 1) && lane == 0) atomicOr(err, 2);
+    } else {
+        // compute warps
+        const unsigned N = (unsigned)L.N;
+        const int r = tid / n0, x = tid - r * n0;
+        const int xm = x == 0 ? n0 - 1 : x - 1, xp = x == n0 - 1 ? 0 : x + 1;
+        const int qb = r * n0, q0 = qb + x, qm = qb + xm, qp = qb + xp;
+        const bool xface = L.bclo[0] != BC_PERIODIC && (x == 0 || x == n0 - 1);
+        const bool yper = L.bclo[1] == BC_PERIODIC;
+        int i = 0;
+        for (int t = blockIdx.x; t < pl.ntiles; t += gridDim.x, i++) {
+            const int s = i % STAGES;
+            if (!bar_wait(&full[s], (i / STAGES) & 1)) {
+                atomicOr(err, 4);
+                break;
+            }
+            const unsigned char* st = smem_rows + (size_t)s * pl.stage_bytes;
+            const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
+            const int y = y0 + r;
+            if (r < pl.TR && y < n1) {
+                const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
+                // nodes on a face are stepped by k_step_faces
+                if (!(xface || (!yper && (y == 0 || y == n1 - 1)))) {
+                    const S* pop = reinterpret_cast<const S*>(st);
+                    const float* gs = reinterpret_cast<const float*>(st + pl.off_geo);
+                    const float* hs = reinterpret_cast<const float*>(st + pl.off_hist);
+                    const Mom4<float>* js = reinterpret_cast<const Mom4<float>*>(st + pl.off_jf);
+                    float sv[Q];
+#pragma unroll
+                    for (int l = 0; l < Q; l++) {
+                        const int cx = cvec(l, 0);
+                        sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
+                    }
+                    GeoT<float> G;
+                    HistT<float> Hp;
+                    G.sg = gs[q0];
+                    G.isg = recip(G.sg);
+#pragma unroll
+                    for (int a = 0; a < 6; a++) G.gi[a] = gs[(1 + a) * NT + q0];
+#pragma unroll
+                    for (int a = 0; a < 18; a++) G.gam[a] = gs[(7 + a) * NT + q0];
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
+                    Hp.A = hs[q0];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) Hp.B[a] = hs[(1 + a) * NT + q0];
+#pragma unroll
+                    for (int a = 0; a < 6; a++) Hp.C[a] = hs[(4 + a) * NT + q0];
+                    // rho u at site (x + cx, y + cy, z + cz): layer cz + 1, row r + 1 + cy
+                    const int jb = n0;  // row r + 1 starts at (r + 1) n0 = qb + n0
+                    float d[9][3];
+#pragma unroll
+                    for (int k = 0; k < 9; k++) {
+                        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+                        const int ip = (cz + 1) * pl.JS + cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qp : qm));
+                        const int im = (1 - cz) * pl.JS - cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qm : qp));
+                        const Mom4<float> p = js[ip], m = js[im];
+                        d[k][0] = p.x - m.x;
+                        d[k][1] = p.y - m.y;
+                        d[k][2] = p.z - m.z;
+                    }
+                    step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
+                }
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) bar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace rows
+
+// one time step through the row-staged pass (the context's plan and maps
+// exist): momentum pass; then the row pass on the stream and, concurrently,
+// the face nodes on the side stream.  Returns the number of kernels launched.
+template <class S>
+int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* err)
+{
+    static bool attr = false;
+    if (!attr) {
+        int max_smem = 0;
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+        cudaFuncSetAttribute(rows::k_step_rows<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        attr = true;
+    }
+    const cslbm_rows& R = c->rows;
+    const rows::Plan& pl = R.plan;
+    const S* Pin = (const S*)c->P[pc];
+    S* Pout = (S*)c->P[1 - pc];
+    const float* hin = (const float*)c->H[hc];
+    float* hout = (float*)c->H[1 - hc];
+    const float* geo = (const float*)c->G[gc];
+    launch_momentum<S, float>(c, L, Pin, hin, geo);
+    int launched = 1;
+    const FaceList f = face_list(c);
+    const bool faces = f.start[f.nseg] > 0;
+    if (faces) {
+        cudaEventRecord(R.fork, c->stream);
+        cudaStreamWaitEvent(R.side, R.fork, 0);
+        launched += launch_faces<S, float>(c, L, Pin, Pout, hin, hout, geo, R.side);
+        cudaEventRecord(R.join, R.side);
+    }
+    if (pl.ntiles > 0) {
+        rows::Maps M;
+        M.pop = R.pop[pc];
+        M.jf = R.jf;
+        M.geo = R.geo[gc];
+        M.hist = R.hist[hc];
+        const int grid = pl.ntiles < c->n_sm ? pl.ntiles : c->n_sm;
+        rows::k_step_rows<S><<<grid, rows::NTHR, rows::smem_bytes(pl), c->stream>>>(L, pl, M, Pin, Pout, hout,
+                                                                                   (const Mom4<float>*)c->jf, err);
+        launched++;
+    }
+    if (faces) cudaStreamWaitEvent(c->stream, R.join, 0);
+    return launched;
+}
+
+}  // namespace cslbm

@@ -1,0 +1,54 @@
+// Shape of the row-staged step pass (host and device): tile size, the byte
+// layout of one shared-memory stage, and whether the pass applies.
+#pragma once
+
+namespace cslbm {
+namespace rows {
+
+constexpr int NT = 256;        // compute threads of a CTA, nodes of a tile at most
+constexpr int NW = NT / 32;    // compute warps
+constexpr int NTHR = NT + 32;  // + the copy warp
+constexpr int STAGES = 2;
+constexpr int NGEO = 25, NHIST = 10;
+
+// A tile is TR whole x-rows of one plane.  In a stage the populations sit at
+// [lambda][NT], rho u at [z-layer][JS] (16-byte nodes), geometry at
+// [25][NT] and history at [10][NT], every block 128-byte aligned.
+struct Plan {
+    int TR;        // rows per tile
+    int nyb;       // tiles per plane
+    int z0;        // first plane that is not a face plane
+    int ntiles;    // nyb * (planes that are not face planes)
+    int JS;        // nodes per rho u layer: (TR + 2) n0 rounded up to 8
+    unsigned off_jf, off_geo, off_hist, stage_bytes;
+};
+
+inline unsigned smem_bytes(const Plan& pl) { return STAGES * pl.stage_bytes + 2 * STAGES * 8; }
+
+// false when the pass does not apply: rows longer than NT nodes or not a
+// whole number of 16-byte chunks, fewer than NT nodes in all, or stages that
+// do not fit in max_smem bytes
+inline bool make_plan(const int n[3], bool zper, int s_bytes, int max_smem, Plan& pl)
+{
+    const long long N = (long long)n[0] * n[1] * n[2];
+    if (n[0] > NT || n[0] % 4 != 0 || (n[0] * s_bytes) % 16 != 0 || N < NT) return false;
+    if (!zper && n[2] < 3) return false;
+    pl.TR = NT / n[0] < n[1] ? NT / n[0] : n[1];
+    pl.nyb = (n[1] + pl.TR - 1) / pl.TR;
+    pl.z0 = zper ? 0 : 1;
+    pl.ntiles = pl.nyb * (zper ? n[2] : n[2] - 2);
+    pl.JS = ((pl.TR + 2) * n[0] + 7) / 8 * 8;
+    unsigned o = ((unsigned)(19 * NT * s_bytes) + 127u) & ~127u;
+    pl.off_jf = o;
+    o += 3u * pl.JS * 16u;
+    o = (o + 127u) & ~127u;
+    pl.off_geo = o;
+    o += NGEO * NT * 4u;
+    pl.off_hist = o;
+    o += NHIST * NT * 4u;
+    pl.stage_bytes = (o + 127u) & ~127u;
+    return (long long)smem_bytes(pl) <= max_smem;
+}
+
+}  // namespace rows
+}  // namespace cslbm

@@ -16,6 +16,7 @@ from . import _abi
 from ._abi import call
 
 STORAGE = {"fp32": _abi.FP32, "fp16": _abi.FP16S, "bf16": _abi.BF16S, "fp64": _abi.FP64}
+STEP_KERNEL = {"auto": _abi.STEP_AUTO, "flat": _abi.STEP_FLAT}
 
 
 def _torch():
@@ -31,11 +32,12 @@ class CurvedLattice:
     bc_lo / bc_hi: per-axis face rules (PERIODIC, WALL, INFLOW, OUTFLOW);
     tau: BGK relaxation time; fext: contravariant body-force density;
     storage: "fp32", "fp16", "bf16" (weight-shifted, FP32 arithmetic) or
-    "fp64"; literal_a2: transform a_(2) itself on chart changes.
+    "fp64"; literal_a2: transform a_(2) itself on chart changes;
+    step_kernel: "auto" (row-staged pass where it applies) or "flat".
     """
 
     def __init__(self, n, bc_lo=(0, 0, 0), bc_hi=None, tau=0.8, theta=0.0, fext=(0.0, 0.0, 0.0),
-                 storage="fp32", literal_a2=False, device=None, stream=None):
+                 storage="fp32", literal_a2=False, step_kernel="auto", device=None, stream=None):
         torch = _torch()
         _abi.load()
         self.n = tuple(int(v) for v in n)
@@ -43,7 +45,8 @@ class CurvedLattice:
         bc_hi = bc_lo if bc_hi is None else bc_hi
         self.params = _abi.Params((ctypes.c_int * 3)(*self.n), (ctypes.c_int * 3)(*bc_lo),
                                   (ctypes.c_int * 3)(*bc_hi), float(tau), float(theta),
-                                  (ctypes.c_double * 3)(*fext), STORAGE[storage], int(bool(literal_a2)))
+                                  (ctypes.c_double * 3)(*fext), STORAGE[storage], int(bool(literal_a2)),
+                                  STEP_KERNEL[step_kernel])
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
         nbytes = ctypes.c_size_t(0)

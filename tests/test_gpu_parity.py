@@ -21,10 +21,11 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
-def make_pair(w, storage, literal=False):
+def make_pair(w, storage, literal=False, step_kernel="auto"):
     from paper_1803_07822_gb300.lattice import CurvedLattice
     kw = dict(tau=w["tau"], fext=w["fext"])
-    g = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], storage=storage, literal_a2=literal, **kw)
+    g = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], storage=storage, literal_a2=literal, step_kernel=step_kernel,
+                      **kw)
     o = oracle.Lattice(w["n"], w["bc_lo"], w["bc_hi"], literal_a2=literal, **kw)
     ch = w["chart"]
     g.set_chart(ch)
@@ -47,18 +48,22 @@ def compare(g, o, J9, tol, tag=""):
 TOL = {"fp64": 1e-11, "fp32": 1e-5}
 
 
-LAYOUTS = [(2, 0, 1), (0, 1, 2)]  # (wall, span, flow): walls on the marching axis / on the fastest axis
+LAYOUTS = [(2, 0, 1), (0, 1, 2)]  # (wall, span, flow): walls across z / across x
+
+# storage and step pass: FP64 always takes the flat pass; FP32 runs both the
+# row-staged pass (auto, where the shape allows it) and the flat pass
+KERNELS = [("fp64", "auto"), ("fp32", "auto"), ("fp32", "flat")]
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_plain_channel_1000_steps(storage, layout):
+@pytest.mark.parametrize("storage,kernel", KERNELS)
+def test_plain_channel_1000_steps(storage, kernel, layout):
     """16x16x32 periodic channel (32 along the flow), static one-mode metric
     (5 %), walls, body force, tau = 0.8, rho = 1, u = 0, 1000 steps."""
     n = [0, 0, 0]
     n[layout[0]], n[layout[1]], n[layout[2]] = 16, 16, 32
     w = I.plain_fp64_channel(tuple(n), layout)
-    g, o = make_pair(w, storage)
+    g, o = make_pair(w, storage, step_kernel=kernel)
     g.init_equilibrium()
     o.init()
     rg, ug = g.moments()
@@ -155,12 +160,13 @@ def test_dynamic_metric_with_transform(literal):
         compare(g, o, ch_old.J9, TOL[storage], storage)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "flat"])
 @pytest.mark.parametrize("storage,tol", [("fp16", 3e-2), ("bf16", 1e-1)])
-def test_reduced_precision_storage_error(storage, tol):
+def test_reduced_precision_storage_error(storage, tol, kernel):
     """Weight-shifted FP16/BF16 storage with FP32 arithmetic, error vs the
     FP64 oracle on the plain channel after 1000 steps (stated bounds)."""
     w = I.plain_fp64_channel()
-    g, o = make_pair(w, storage)
+    g, o = make_pair(w, storage, step_kernel=kernel)
     g.init_equilibrium()
     o.init()
     g.step(1000)
@@ -217,14 +223,19 @@ def test_host_and_device_inputs_agree_and_state_roundtrip():
     assert a.check()
 
 
-# Lattices with n0 % 32 == 0 and n1 % 8 == 0 take the bulk-copy step kernel
-# (FP32 storage); the cases cover one x-tile (both periodic wraps in one
-# CTA), two x-tiles, walls across x, walls across z and inflow/outflow.
+# Shapes for the row-staged step pass (FP32 storage, n0 a multiple of 4 and
+# at most 256; a tile is floor(256 / n0) whole x-rows of one plane): a ragged
+# last tile per plane, one 256-node row per tile, rows that straddle warps,
+# walls across x (face lanes inside staged rows), periodic flow, and a
+# lattice periodic on all three axes (every wrap of the row copies).
 TILED = [
-    ("span-x one tile", (32, 24, 12), (2, 0, 1), "inout"),
+    ("ragged last tile", (20, 29, 13), (2, 0, 1), "inout"),
+    ("one row per tile", (256, 24, 12), (2, 0, 1), "inout"),
+    ("rows straddle warps", (100, 24, 10), (2, 0, 1), "periodic"),
     ("span-x two tiles", (64, 16, 9), (2, 0, 1), "inout"),
     ("walls across x", (32, 16, 40), (0, 1, 2), "inout"),
     ("periodic flow", (32, 32, 16), (2, 0, 1), "periodic"),
+    ("periodic everywhere", (8, 6, 7), None, "torus"),
 ]
 
 
@@ -238,22 +249,30 @@ def smooth_wall_velocity(n, layout, amp=0.005):
     return u
 
 
-@pytest.mark.parametrize("name,n,layout,kind", TILED, ids=[t[0] for t in TILED])
-def test_tiled_fp32_fast_path(name, n, layout, kind):
-    rng = np.random.default_rng(11)
+def tiled_case(n, layout, kind):
+    if kind == "torus":
+        ch = I.flat_chart(n)
+        return dict(n=n, bc_lo=(P, P, P), bc_hi=(P, P, P), tau=0.6, fext=(1e-5, -2e-5, 1e-5), chart=ch)
     if kind == "periodic":
         w = I.periodic_channel(n, 0.7, 0.04, 3, 0.05, 12, layout=layout)
         w["faces"] = {(layout[0], 1): smooth_wall_velocity(n, layout)}
-    else:
-        dfm = I.fourier_deformation(n, 4, 0.06, seed=13, flow_periodic=False, kmax=2, lmax=1, layout=layout)
-        ch = I.channel_chart(n, dfm, layout)
-        lo, hi = [P] * 3, [P] * 3
-        lo[layout[0]] = hi[layout[0]] = W
-        lo[layout[2]], hi[layout[2]] = IN, OUT
-        w = dict(n=n, bc_lo=tuple(lo), bc_hi=tuple(hi), tau=0.65, fext=(0.0, 0.0, 0.0), chart=ch,
-                 faces={(layout[2], 0): I.inflow_profile(n, ch, 0.04, layout),
-                        (layout[0], 1): smooth_wall_velocity(n, layout)})
-    g, o = make_pair(w, "fp32")
+        return w
+    dfm = I.fourier_deformation(n, 4, 0.06, seed=13, flow_periodic=False, kmax=2, lmax=1, layout=layout)
+    ch = I.channel_chart(n, dfm, layout)
+    lo, hi = [P] * 3, [P] * 3
+    lo[layout[0]] = hi[layout[0]] = W
+    lo[layout[2]], hi[layout[2]] = IN, OUT
+    return dict(n=n, bc_lo=tuple(lo), bc_hi=tuple(hi), tau=0.65, fext=(0.0, 0.0, 0.0), chart=ch,
+                faces={(layout[2], 0): I.inflow_profile(n, ch, 0.04, layout),
+                       (layout[0], 1): smooth_wall_velocity(n, layout)})
+
+
+@pytest.mark.parametrize("kernel", ["auto", "flat"])
+@pytest.mark.parametrize("name,n,layout,kind", TILED, ids=[t[0] for t in TILED])
+def test_tiled_fp32(name, n, layout, kind, kernel):
+    rng = np.random.default_rng(11)
+    w = tiled_case(n, layout, kind)
+    g, o = make_pair(w, "fp32", step_kernel=kernel)
     N = int(np.prod(n))
     rho0 = 1 + 0.005 * rng.standard_normal(N)
     u0 = 0.01 * rng.standard_normal((3, N))
@@ -263,3 +282,19 @@ def test_tiled_fp32_fast_path(name, n, layout, kind):
     o.step(120)
     assert g.check()
     compare(g, o, w["chart"].J9, TOL["fp32"], name)
+
+
+@pytest.mark.parametrize("name,n,layout,kind", TILED[:3], ids=[t[0] for t in TILED[:3]])
+def test_row_staged_and_flat_passes_agree(name, n, layout, kind):
+    """The two step passes compute the same arithmetic in the same order per
+    node; after 50 steps they agree to FP32 rounding."""
+    w = tiled_case(n, layout, kind)
+    a, _ = make_pair(w, "fp32", step_kernel="auto")
+    b, _ = make_pair(w, "fp32", step_kernel="flat")
+    a.init_equilibrium()
+    b.init_equilibrium()
+    a.step(50)
+    b.step(50)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert rel(ra, rb) < 1e-6 and rel(ua, ub) < 1e-5
