@@ -196,8 +196,8 @@ cslbm_status cslbm_record_error(cslbm_status s, const char* msg) { return fail(s
 
 namespace {
 
-// The row-staged step pass: plan, tensor maps and side stream, when the
-// storage, shape and device allow it (otherwise the flat pass serves).
+// The row-staged step pass: plan and tensor maps, when the storage, shape
+// and device allow it (otherwise the flat pass serves).
 void rows_prepare(cslbm_ctx* c)
 {
     cslbm_rows& R = c->rows;
@@ -241,27 +241,7 @@ void rows_prepare(cslbm_ctx* c)
     const cuuint32_t jb[4] = {4, (cuuint32_t)n0, TR + 2, 1};
     ok = ok && mk(&R.jf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->jf, jd, js, jb);
     if (!ok) return;
-    if (cudaStreamCreateWithFlags(&R.side, cudaStreamNonBlocking) != cudaSuccess) return;
-    if (cudaEventCreateWithFlags(&R.fork, cudaEventDisableTiming) != cudaSuccess) {
-        cudaStreamDestroy(R.side);
-        return;
-    }
-    if (cudaEventCreateWithFlags(&R.join, cudaEventDisableTiming) != cudaSuccess) {
-        cudaEventDestroy(R.fork);
-        cudaStreamDestroy(R.side);
-        return;
-    }
     R.ok = 1;
-}
-
-void rows_release(cslbm_ctx* c)
-{
-    if (!c->rows.ok) return;
-    cudaStreamSynchronize(c->rows.side);
-    cudaEventDestroy(c->rows.fork);
-    cudaEventDestroy(c->rows.join);
-    cudaStreamDestroy(c->rows.side);
-    c->rows.ok = 0;
 }
 
 }  // namespace
@@ -338,7 +318,6 @@ cslbm_status cslbm_destroy(cslbm_ctx* c)
     if (!c) return fail(CSLBM_EINVAL, "ctx is null");
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    rows_release(c);
     delete c;
     return CSLBM_OK;
 }

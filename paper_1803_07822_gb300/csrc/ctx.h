@@ -14,9 +14,8 @@
 struct cslbm_ops;
 
 // Resources of the row-staged step pass, made at creation when it applies:
-// its plan, tensor maps of the buffers it stages (populations and history
-// per ping-pong buffer), and a side stream on which the face nodes are
-// stepped while the row pass runs.
+// its plan and the tensor maps of the buffers it stages (populations,
+// geometry and history per ping-pong buffer, rho u).
 struct cslbm_rows {
     int ok;
     cslbm::rows::Plan plan;
@@ -24,8 +23,6 @@ struct cslbm_rows {
     CUtensorMap jf;       // [n2][n1][n0][4] rho u, box 4 x n0 x (TR + 2)
     CUtensorMap geo[2];   // [25][N] geometry, box NT x 25
     CUtensorMap hist[2];  // [10][N] history, box NT x 10
-    cudaStream_t side;
-    cudaEvent_t fork, join;
 };
 
 struct cslbm_ctx {

@@ -113,30 +113,40 @@ __global__ void __launch_bounds__(TB) k_momentum_flat(Lat L, const S* __restrict
 
 // rho u at a stencil site that may lie one step outside a non-periodic face:
 // linear extrapolation 2 j(face) - j(face - normal) per out-of-range axis
+// (tensor product over the axes).  Each axis contributes one or two
+// (coordinate, weight) terms; the 2 x 2 x 2 sum is unrolled with the loads of
+// zero-weight terms predicated off, so that all loads can be in flight at once.
+__device__ __forceinline__ void site_axis(int r, int n, bool per_lo, bool per_hi, int& c0, int& c1, float& w0, float& w1)
+{
+    if (r >= 0 && r < n) { c0 = c1 = r; w0 = 1.0f; w1 = 0.0f; }
+    else if (r < 0 && per_lo) { c0 = c1 = r + n; w0 = 1.0f; w1 = 0.0f; }
+    else if (r >= n && per_hi) { c0 = c1 = r - n; w0 = 1.0f; w1 = 0.0f; }
+    else if (r < 0) { c0 = 0; c1 = 1; w0 = 2.0f; w1 = -1.0f; }
+    else { c0 = n - 1; c1 = n - 2; w0 = 2.0f; w1 = -1.0f; }
+}
 template <class R>
 __device__ __forceinline__ Mom4<R> mom_site(const Lat& L, const Mom4<R>* __restrict__ jf, int x, int y, int z)
 {
-    int r[3] = {x, y, z}, c0[3], c1[3], nopt[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const int n = L.n[a];
-        c1[a] = 0;
-        if (r[a] >= 0 && r[a] < n) { c0[a] = r[a]; nopt[a] = 1; }
-        else if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) { c0[a] = wrapc(r[a], n); nopt[a] = 1; }
-        else if (r[a] < 0) { c0[a] = 0; c1[a] = 1; nopt[a] = 2; }
-        else { c0[a] = n - 1; c1[a] = n - 2; nopt[a] = 2; }
-    }
+    int x0, x1, y0, y1, z0, z1;
+    float wx0, wx1, wy0, wy1, wz0, wz1;
+    site_axis(x, L.n[0], L.bclo[0] == BC_PERIODIC, L.bchi[0] == BC_PERIODIC, x0, x1, wx0, wx1);
+    site_axis(y, L.n[1], L.bclo[1] == BC_PERIODIC, L.bchi[1] == BC_PERIODIC, y0, y1, wy0, wy1);
+    site_axis(z, L.n[2], L.bclo[2] == BC_PERIODIC, L.bchi[2] == BC_PERIODIC, z0, z1, wz0, wz1);
     Mom4<R> acc;
     acc.x = acc.y = acc.z = acc.w = R(0);
-    for (int i = 0; i < nopt[0]; i++)
-        for (int k = 0; k < nopt[1]; k++)
-            for (int m = 0; m < nopt[2]; m++) {
-                const R wt = (i ? R(-1) : (nopt[0] == 2 ? R(2) : R(1))) * (k ? R(-1) : (nopt[1] == 2 ? R(2) : R(1))) *
-                             (m ? R(-1) : (nopt[2] == 2 ? R(2) : R(1)));
-                const Mom4<R> j = jf[nidx(L, i ? c1[0] : c0[0], k ? c1[1] : c0[1], m ? c1[2] : c0[2])];
-                acc.x += wt * j.x;
-                acc.y += wt * j.y;
-                acc.z += wt * j.z;
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                const float w = (i ? wx1 : wx0) * (k ? wy1 : wy0) * (m ? wz1 : wz0);
+                if (w != 0.0f) {
+                    const Mom4<R> j = jf[nidx(L, i ? x1 : x0, k ? y1 : y0, m ? z1 : z0)];
+                    acc.x += R(w) * j.x;
+                    acc.y += R(w) * j.y;
+                    acc.z += R(w) * j.z;
+                }
             }
     return acc;
 }
@@ -197,9 +207,10 @@ __device__ __forceinline__ void load_geo_hist(const R* __restrict__ geo, const R
 
 // the step of a node on a non-periodic face (boundary rule, ghost stencil)
 template <class S, class R>
-__device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ Pin, S* __restrict__ Pout,
-                                           const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ geo,
-                                           const Mom4<R>* __restrict__ jf, int x, int y, int z)
+__device__ __forceinline__ void step_boundary_body(const Lat& L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                   const R* __restrict__ hin, R* __restrict__ hout,
+                                                   const R* __restrict__ geo, const Mom4<R>* __restrict__ jf, int x,
+                                                   int y, int z)
 {
     const unsigned N = (unsigned)L.N, v = (unsigned)nidx(L, x, y, z);
     R s[Q];
@@ -208,6 +219,7 @@ __device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ P
     HistT<R> Hp;
     load_geo_hist(geo, hin, v, N, G, Hp);
     R d[9][3];
+#pragma unroll
     for (int k = 0; k < 9; k++) {
         const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
         const Mom4<R> p = mom_site(L, jf, x + cx, y + cy, z + cz), m = mom_site(L, jf, x - cx, y - cy, z - cz);
@@ -216,6 +228,15 @@ __device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ P
         d[k][2] = p.z - m.z;
     }
     step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
+}
+
+// out of line where face nodes share a kernel with interior nodes
+template <class S, class R>
+__device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                           const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ geo,
+                                           const Mom4<R>* __restrict__ jf, int x, int y, int z)
+{
+    step_boundary_body<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
 }
 
 template <class S, class R>
@@ -300,14 +321,26 @@ __global__ void __launch_bounds__(128) k_step_faces(const __grid_constant__ Lat 
 {
     const long long i = blockIdx.x * 128LL + threadIdx.x;
     if (i >= f.start[f.nseg]) return;
-    int k = 0;
-    while (k + 1 < f.nseg && i >= f.start[k + 1]) k++;
-    const long long r = i - f.start[k];
-    const int x = f.lo[k][0] + (int)(r % f.len[k][0]);
-    const long long q = r / f.len[k][0];
-    const int y = f.lo[k][1] + (int)(q % f.len[k][1]);
-    const int z = f.lo[k][2] + (int)(q / f.len[k][1]);
-    step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
+    // segment of node i, by selects over the six (no indexing of f by a
+    // runtime value, which would copy it to local memory)
+    int lo0 = 0, lo1 = 0, lo2 = 0, len0 = 1, len1 = 1;
+    long long st = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        if (k < f.nseg && i >= f.start[k]) {
+            lo0 = f.lo[k][0];
+            lo1 = f.lo[k][1];
+            lo2 = f.lo[k][2];
+            len0 = f.len[k][0];
+            len1 = f.len[k][1];
+            st = f.start[k];
+        }
+    const long long r = i - st;
+    const long long q = r / len0;
+    const int x = lo0 + (int)(r - q * len0);
+    const int y = lo1 + (int)(q % len1);
+    const int z = lo2 + (int)(q / len1);
+    step_boundary_body<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
 }
 
 template <class S, class R>

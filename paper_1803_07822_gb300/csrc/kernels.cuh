@@ -3,6 +3,8 @@
 // format by the inst_*.cu units, which instantiate the ops table.
 #pragma once
 
+#include <type_traits>
+
 #include "ctx.h"
 #include "flat_step.cuh"
 #include "row_step.cuh"
@@ -60,9 +62,28 @@ __global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, c
         atomicOr(bad, 1);
         return;
     }
-    const double id = 1.0 / det;
+    // 1/det and sqrt(det) in FP64.  For FP32-and-narrower storage they start
+    // from FP32 estimates refined by one Newton step each (relative error
+    // ~1e-14 before the rounding to R), which spares the FP64 divide and
+    // square root; FP64 storage divides exactly.
+    double id, sd;
+    if constexpr (std::is_same<R, double>::value) {
+        id = 1.0 / det;
+        sd = sqrt(det);
+    } else {
+        if (det > 1e-30 && det < 1e30) {
+            const double r0 = (double)__frcp_rn((float)det);
+            id = fma(r0, fma(-det, r0, 1.0), r0);          // r0 (2 - det r0)
+            const double y0 = (double)rsqrtf((float)det);  // ~ 1/sqrt(det)
+            const double s0 = det * y0;
+            sd = fma(0.5 * y0, fma(-s0, s0, det), s0);     // s0 + (det - s0^2) / (2 s0)
+        } else {
+            id = 1.0 / det;
+            sd = sqrt(det);
+        }
+    }
     double gi[6] = {A * id, B * id, C * id, (a * f - c * c) * id, (b * c - a * e) * id, (a * d - b * b) * id};
-    geo[v] = R(sqrt(det));
+    geo[v] = R(sd);
 #pragma unroll
     for (int k = 0; k < 6; k++) geo[(1 + k) * N + v] = R(gi[k]);
     R dg[3][6], gr[6];
@@ -291,35 +312,43 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
     const R sgo = geo_old[v];
     NodeMoments<S, R> M;
     node_moments<S, R>(L, Pin, hin, geo_old, x, y, z, v, sgo, M);
-    // D phi in FP64: Jnew^-1 Jold
+    // D phi = Jnew^-1 Jold, in FP64 for FP64 storage and in FP32 otherwise
+    // (the FP64 Jacobians rounded; D phi is stored at the precision of R)
+    using Cm = R;
     double Jo[9], Jn[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
         Jo[k] = J[k * L.N + v];
         Jn[k] = Jnew[k * stride + t];
     }
-    double inv[9];
+    Cm n[9], o[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        n[k] = Cm(Jn[k]);
+        o[k] = Cm(Jo[k]);
+    }
+    Cm inv[9];
     {
-        const double c00 = Jn[4] * Jn[8] - Jn[5] * Jn[7], c01 = Jn[5] * Jn[6] - Jn[3] * Jn[8], c02 = Jn[3] * Jn[7] - Jn[4] * Jn[6];
-        const double det = Jn[0] * c00 + Jn[1] * c01 + Jn[2] * c02, id = 1.0 / det;
+        const Cm c00 = n[4] * n[8] - n[5] * n[7], c01 = n[5] * n[6] - n[3] * n[8], c02 = n[3] * n[7] - n[4] * n[6];
+        const Cm det = n[0] * c00 + n[1] * c01 + n[2] * c02, id = Cm(1) / det;
         inv[0] = c00 * id;
         inv[3] = c01 * id;
         inv[6] = c02 * id;
-        inv[1] = (Jn[2] * Jn[7] - Jn[1] * Jn[8]) * id;
-        inv[4] = (Jn[0] * Jn[8] - Jn[2] * Jn[6]) * id;
-        inv[7] = (Jn[1] * Jn[6] - Jn[0] * Jn[7]) * id;
-        inv[2] = (Jn[1] * Jn[5] - Jn[2] * Jn[4]) * id;
-        inv[5] = (Jn[2] * Jn[3] - Jn[0] * Jn[5]) * id;
-        inv[8] = (Jn[0] * Jn[4] - Jn[1] * Jn[3]) * id;
+        inv[1] = (n[2] * n[7] - n[1] * n[8]) * id;
+        inv[4] = (n[0] * n[8] - n[2] * n[6]) * id;
+        inv[7] = (n[1] * n[6] - n[0] * n[7]) * id;
+        inv[2] = (n[1] * n[5] - n[2] * n[4]) * id;
+        inv[5] = (n[2] * n[3] - n[0] * n[5]) * id;
+        inv[8] = (n[0] * n[4] - n[1] * n[3]) * id;
     }
     R Dp[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            double s = 0.0;
+            Cm s = Cm(0);
 #pragma unroll
-            for (int m = 0; m < 3; m++) s += inv[i * 3 + m] * Jo[m * 3 + k];
+            for (int m = 0; m < 3; m++) s += inv[i * 3 + m] * o[m * 3 + k];
             Dp[i][k] = R(s);
         }
 #pragma unroll

@@ -257,54 +257,57 @@ __global__ void __launch_bounds__(NTHR, 1)
             const unsigned char* st = smem_rows + (size_t)s * pl.stage_bytes;
             const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
             const int y = y0 + r;
-            if (r < pl.TR && y < n1) {
-                const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
-                // nodes on a face are stepped by k_step_faces
-                if (!(xface || (!yper && (y == 0 || y == n1 - 1)))) {
-                    const S* pop = reinterpret_cast<const S*>(st);
-                    const float* gs = reinterpret_cast<const float*>(st + pl.off_geo);
-                    const float* hs = reinterpret_cast<const float*>(st + pl.off_hist);
-                    const Mom4<float>* js = reinterpret_cast<const Mom4<float>*>(st + pl.off_jf);
-                    float sv[Q];
+            // nodes on a face are stepped by k_step_faces
+            const bool active = r < pl.TR && y < n1 && !(xface || (!yper && (y == 0 || y == n1 - 1)));
+            // every input of the node into registers first, so that the stage
+            // goes back to the copy warp before the arithmetic starts
+            float sv[Q];
+            GeoT<float> G;
+            HistT<float> Hp;
+            float d[9][3];
+            if (active) {
+                const S* pop = reinterpret_cast<const S*>(st);
+                const float* gs = reinterpret_cast<const float*>(st + pl.off_geo);
+                const float* hs = reinterpret_cast<const float*>(st + pl.off_hist);
+                const Mom4<float>* js = reinterpret_cast<const Mom4<float>*>(st + pl.off_jf);
 #pragma unroll
-                    for (int l = 0; l < Q; l++) {
-                        const int cx = cvec(l, 0);
-                        sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
-                    }
-                    GeoT<float> G;
-                    HistT<float> Hp;
-                    G.sg = gs[q0];
-                    G.isg = recip(G.sg);
+                for (int l = 0; l < Q; l++) {
+                    const int cx = cvec(l, 0);
+                    sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
+                }
+                G.sg = gs[q0];
 #pragma unroll
-                    for (int a = 0; a < 6; a++) G.gi[a] = gs[(1 + a) * NT + q0];
+                for (int a = 0; a < 6; a++) G.gi[a] = gs[(1 + a) * NT + q0];
 #pragma unroll
-                    for (int a = 0; a < 18; a++) G.gam[a] = gs[(7 + a) * NT + q0];
+                for (int a = 0; a < 18; a++) G.gam[a] = gs[(7 + a) * NT + q0];
+                Hp.A = hs[q0];
 #pragma unroll
-                    for (int k = 0; k < 3; k++)
-                        G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
-                    Hp.A = hs[q0];
+                for (int a = 0; a < 3; a++) Hp.B[a] = hs[(1 + a) * NT + q0];
 #pragma unroll
-                    for (int a = 0; a < 3; a++) Hp.B[a] = hs[(1 + a) * NT + q0];
+                for (int a = 0; a < 6; a++) Hp.C[a] = hs[(4 + a) * NT + q0];
+                // rho u at site (x + cx, y + cy, z + cz): layer cz + 1, row r + 1 + cy
+                const int jb = n0;  // row r + 1 starts at (r + 1) n0 = qb + n0
 #pragma unroll
-                    for (int a = 0; a < 6; a++) Hp.C[a] = hs[(4 + a) * NT + q0];
-                    // rho u at site (x + cx, y + cy, z + cz): layer cz + 1, row r + 1 + cy
-                    const int jb = n0;  // row r + 1 starts at (r + 1) n0 = qb + n0
-                    float d[9][3];
-#pragma unroll
-                    for (int k = 0; k < 9; k++) {
-                        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-                        const int ip = (cz + 1) * pl.JS + cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qp : qm));
-                        const int im = (1 - cz) * pl.JS - cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qm : qp));
-                        const Mom4<float> p = js[ip], m = js[im];
-                        d[k][0] = p.x - m.x;
-                        d[k][1] = p.y - m.y;
-                        d[k][2] = p.z - m.z;
-                    }
-                    step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
+                for (int k = 0; k < 9; k++) {
+                    const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+                    const int ip = (cz + 1) * pl.JS + cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qp : qm));
+                    const int im = (1 - cz) * pl.JS - cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qm : qp));
+                    const Mom4<float> p = js[ip], m = js[im];
+                    d[k][0] = p.x - m.x;
+                    d[k][1] = p.y - m.y;
+                    d[k][2] = p.z - m.z;
                 }
             }
             __syncwarp();
             if ((tid & 31) == 0) bar_arrive(&empty[s]);
+            if (active) {
+                G.isg = recip(G.sg);
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
+                const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
+                step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
+            }
         }
     }
     __syncthreads();
@@ -313,8 +316,8 @@ __global__ void __launch_bounds__(NTHR, 1)
 }  // namespace rows
 
 // one time step through the row-staged pass (the context's plan and maps
-// exist): momentum pass; then the row pass on the stream and, concurrently,
-// the face nodes on the side stream.  Returns the number of kernels launched.
+// exist): momentum pass, row pass, face nodes.  Returns the number of
+// kernels launched.
 template <class S>
 int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* err)
 {
@@ -334,14 +337,6 @@ int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, i
     const float* geo = (const float*)c->G[gc];
     launch_momentum<S, float>(c, L, Pin, hin, geo);
     int launched = 1;
-    const FaceList f = face_list(c);
-    const bool faces = f.start[f.nseg] > 0;
-    if (faces) {
-        cudaEventRecord(R.fork, c->stream);
-        cudaStreamWaitEvent(R.side, R.fork, 0);
-        launched += launch_faces<S, float>(c, L, Pin, Pout, hin, hout, geo, R.side);
-        cudaEventRecord(R.join, R.side);
-    }
     if (pl.ntiles > 0) {
         rows::Maps M;
         M.pop = R.pop[pc];
@@ -353,7 +348,7 @@ int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, i
                                                                                    (const Mom4<float>*)c->jf, err);
         launched++;
     }
-    if (faces) cudaStreamWaitEvent(c->stream, R.join, 0);
+    launched += launch_faces<S, float>(c, L, Pin, Pout, hin, hout, geo, c->stream);
     return launched;
 }
 
