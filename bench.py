@@ -48,14 +48,22 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
 # the same channel, FP32 storage; both passes touch every node once, so the
 # per-launch traffic scales with the node count.  Only valid for the kernels
 # as they were captured.
-MEASURED_DRAM_BYTES_PER_NODE = {"fp32": (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
+MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
 
 
-def row_staged(n, storage, step_kernel):
-    """Whether the library takes the row-staged step pass for this lattice
-    (the rule include/cslbm.h states for CSLBM_STEP_AUTO)."""
+def step_pass(n, storage, step_kernel, axis2_periodic=False):
+    """The step pass the library takes for this lattice (the rule
+    include/cslbm.h states for cslbm_step_kernel): "fused", "rows" or "flat"."""
     sb = {"fp32": 4, "fp16": 2, "bf16": 2}.get(storage)
-    return step_kernel == "auto" and sb is not None and n[0] <= 256 and n[0] % 4 == 0 and (n[0] * sb) % 16 == 0
+    rows = (step_kernel in ("auto", "rows") and sb is not None and n[0] <= 256 and n[0] % 4 == 0
+            and (n[0] * sb) % 16 == 0 and n[0] * n[1] * n[2] >= 256)
+    if rows and step_kernel == "auto" and not axis2_periodic:
+        return "fused"
+    return "rows" if rows else "flat"
+
+
+PASS_KERNELS = {"fused": "k_step_fused + k_step_faces", "rows": "k_momentum_flat + k_step_rows + k_step_faces",
+                "flat": "k_momentum_flat + k_step_flat"}
 
 
 def workload_spec(name):
@@ -219,7 +227,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--snapshots", type=int, default=3)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "flat"])
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -289,8 +297,8 @@ def main():
     step_ms = step_ms_total / max(nprof, 1)
     bpn = BYTES_PER_NODE[spec["storage"]]
     achieved = bpn * N / (step_ms * 1e-3) / 1e9
-    rows = row_staged(spec["n"], spec["storage"], args.step_kernel)
-    mb = None if rows else MEASURED_DRAM_BYTES_PER_NODE.get(spec["storage"])
+    sp = step_pass(spec["n"], spec["storage"], args.step_kernel)
+    mb = MEASURED_DRAM_BYTES_PER_NODE.get((sp, spec["storage"]))
     traffic = None if mb is None else mb * N
     e2e = None if args.no_e2e else end_to_end(args, lat, snaps, N, world)
     line = {
@@ -302,7 +310,7 @@ def main():
                    "state_finite_after_run": ok},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "one LBM step: k_momentum_flat + " + ("k_step_rows" if rows else "k_step_flat"), "bytes_per_node": bpn,
+                     "kernel": "one LBM step: " + PASS_KERNELS[sp], "bytes_per_node": bpn,
                      "step_ms": step_ms},
         "e2e": e2e,
         "gpu_launches": launches,

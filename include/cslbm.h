@@ -70,11 +70,16 @@ typedef struct {
     int step_kernel;    /* cslbm_step_kernel: which step pass runs (same results up to rounding) */
 } cslbm_params;
 
-/* Step pass.  AUTO takes the row-staged pass (whole lattice rows copied to
- * shared memory by the bulk-copy engine) where it applies -- FP32/FP16/BF16
- * storage, n[0] <= 256 and n[0] * bytes per stored population a multiple of
- * 16 -- and the flat gather pass elsewhere; FLAT always takes the flat pass. */
-typedef enum { CSLBM_STEP_AUTO = 0, CSLBM_STEP_FLAT = 1 } cslbm_step_kernel;
+/* Step pass.  The row-staged pass copies whole lattice rows to shared memory
+ * with the bulk-copy engine; it applies to FP32/FP16/BF16 storage with
+ * n[0] <= 256, n[0] a multiple of 4, n[0] * bytes per stored population a
+ * multiple of 16 and at least 256 nodes.  Its fused form also forms the
+ * momentum field in the same (cooperative) launch; it needs axis 2 to be
+ * non-periodic.  AUTO takes the fused row pass, else the row pass, else the
+ * flat gather pass; ROWS the row pass (momentum field in a kernel of its
+ * own), else the flat pass; FLAT always the flat pass.  All give the same
+ * results up to rounding. */
+typedef enum { CSLBM_STEP_AUTO = 0, CSLBM_STEP_FLAT = 1, CSLBM_STEP_ROWS = 2 } cslbm_step_kernel;
 
 typedef struct cslbm_ctx cslbm_ctx;
 

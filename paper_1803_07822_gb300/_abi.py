@@ -13,7 +13,7 @@ from . import buildlib as _build
 
 OK, EINVAL, ECUDA, ENOMEM, EUNSTABLE, ETIMEOUT, ESTATE = range(7)
 FP32, FP16S, BF16S, FP64 = range(4)
-STEP_AUTO, STEP_FLAT = range(2)
+STEP_AUTO, STEP_FLAT, STEP_ROWS = range(3)
 PERIODIC, WALL, INFLOW, OUTFLOW = range(4)
 
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "EUNSTABLE", 5: "ETIMEOUT", 6: "ESTATE"}

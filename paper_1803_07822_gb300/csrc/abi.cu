@@ -36,7 +36,7 @@ constexpr int kStagingDoubles = 24;           // per node: g6 + dg18
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t off_P[2], off_H[2], off_G[2], off_J, off_jf, off_face[6], off_scratch, off_staging, total;
+    size_t off_P[2], off_H[2], off_G[2], off_J, off_jf, off_face[6], off_scratch, off_done, off_staging, total;
     size_t s_bytes, r_bytes;
     long long N, chunk, face_n[6];
 };
@@ -68,7 +68,7 @@ cslbm_status validate(const cslbm_params* p)
     }
     if (!(p->tau > 0.5)) return fail(CSLBM_EINVAL, "tau must exceed 1/2");
     if (!ops_for(p->storage)) return fail(CSLBM_EINVAL, "unknown storage format");
-    if (p->step_kernel != CSLBM_STEP_AUTO && p->step_kernel != CSLBM_STEP_FLAT)
+    if (p->step_kernel != CSLBM_STEP_AUTO && p->step_kernel != CSLBM_STEP_FLAT && p->step_kernel != CSLBM_STEP_ROWS)
         return fail(CSLBM_EINVAL, "unknown step kernel");
     if (p->n[2] > 65535) return fail(CSLBM_EINVAL, "n[2] must be at most 65535 (one launch row per plane)");
     // the step kernel indexes fields with 32-bit offsets (25 components of N)
@@ -98,6 +98,7 @@ Layout layout(const cslbm_params* p)
         if (!periodic) o += al(3 * L.face_n[k] * sizeof(double));
     }
     L.off_scratch = o; o += al(64 * sizeof(double));
+    L.off_done = o; o += al((size_t)p->n[1] * p->n[2] * sizeof(unsigned));
     L.off_staging = o; o += al(kStagingDoubles * L.chunk * sizeof(double));
     L.total = o;
     return L;
@@ -202,7 +203,9 @@ void rows_prepare(cslbm_ctx* c)
 {
     cslbm_rows& R = c->rows;
     R.ok = 0;
-    if (c->p.step_kernel != CSLBM_STEP_AUTO || c->p.storage == CSLBM_FP64) return;
+    R.fused_ok = 0;
+    R.epoch = 0;
+    if (c->p.step_kernel == CSLBM_STEP_FLAT || c->p.storage == CSLBM_FP64) return;
     int max_smem = 0;
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return;
     if (!cslbm::rows::make_plan(c->n, c->p.bc_lo[2] == CSLBM_PERIODIC, (int)c->s_bytes, max_smem, R.plan)) return;
@@ -236,12 +239,26 @@ void rows_prepare(cslbm_ctx* c)
         const cuuint64_t hd[2] = {N, 10};
         const cuuint32_t hb[2] = {NT, 10};
         ok = ok && mk(&R.hist[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->H[k], hd, gs, hb);
+        const cuuint32_t g1b[2] = {NT, 1}, h4b[2] = {NT, 4};
+        ok = ok && mk(&R.geo1[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->G[k], gd, gs, g1b);
+        ok = ok && mk(&R.hist4[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->H[k], hd, gs, h4b);
     }
-    const cuuint64_t jd[4] = {4, n0, n1, n2}, js[3] = {16, 16 * n0, 16 * n0 * n1};
-    const cuuint32_t jb[4] = {4, (cuuint32_t)n0, TR + 2, 1};
-    ok = ok && mk(&R.jf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->jf, jd, js, jb);
+    // rho u viewed as lines of JL floats, so that the TR + 2 contiguous rows of
+    // a layer are JR lines of up to 1 KB (a view with one 16-byte node per
+    // line would make the copy engine move hundreds of 16-byte lines)
+    const cuuint64_t JL = R.plan.JL;
+    const cuuint64_t jd[2] = {JL, 4 * N / JL}, js[1] = {JL * 4};
+    const cuuint32_t jb[2] = {(cuuint32_t)JL, (cuuint32_t)R.plan.JR};
+    ok = ok && mk(&R.jf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->jf, jd, js, jb);
     if (!ok) return;
     R.ok = 1;
+    // the fused form: momentum and step in one cooperative launch
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (c->p.step_kernel == CSLBM_STEP_AUTO && coop && c->p.bc_lo[2] != CSLBM_PERIODIC &&
+        cslbm::rows::fused_layout(R.plan, (int)c->s_bytes, max_smem, R.off_m, R.off_sg, R.off_h4, R.off_js,
+                                  R.fused_bytes))
+        R.fused_ok = 1;
 }
 
 }  // namespace
@@ -288,6 +305,7 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
         c->face_n[k] = L.face_n[k];
     }
     c->scratch = (double*)(b + L.off_scratch);
+    c->rows.done = (unsigned*)(b + L.off_done);
     c->staging = (double*)(b + L.off_staging);
     c->chunk = L.chunk;
     c->pc = c->hc = c->gc = 0;
@@ -499,6 +517,12 @@ cslbm_status cslbm_check(cslbm_ctx* c)
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         if (terr) {
             CUDA_TRY(cudaMemsetAsync(step_error_flag(c), 0, sizeof(int), c->stream));
+            // the fused pass's publication counts are no longer in step with
+            // its launch count: start both again
+            if (c->rows.ok) {
+                CUDA_TRY(cudaMemsetAsync(c->rows.done, 0, (size_t)c->n[1] * c->n[2] * sizeof(unsigned), c->stream));
+                c->rows.epoch = 0;
+            }
             char m[96];
             snprintf(m, sizeof m, "a bounded wait of the row-staged step pass ran out (code %d)", terr);
             return fail(CSLBM_ETIMEOUT, m);

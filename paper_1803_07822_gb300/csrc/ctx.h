@@ -17,12 +17,18 @@ struct cslbm_ops;
 // its plan and the tensor maps of the buffers it stages (populations,
 // geometry and history per ping-pong buffer, rho u).
 struct cslbm_rows {
-    int ok;
+    int ok;        // the row pass applies (plan and maps made)
+    int fused_ok;  // ... and the fused form (non-periodic axis 2, cooperative launch, smem)
     cslbm::rows::Plan plan;
     CUtensorMap pop[2];   // [19][n2][n1][n0] populations, box n0 x TR
-    CUtensorMap jf;       // [n2][n1][n0][4] rho u, box 4 x n0 x (TR + 2)
+    CUtensorMap jf;       // rho u as [4 N / JL][JL] floats, box JL x JR (the TR + 2 rows of a layer)
     CUtensorMap geo[2];   // [25][N] geometry, box NT x 25
     CUtensorMap hist[2];  // [10][N] history, box NT x 10
+    CUtensorMap geo1[2];  // sqrt(g) alone, box NT x 1
+    CUtensorMap hist4[2]; // A and B of the history, box NT x 4
+    unsigned* done;       // [iterations] CTAs that published each momentum iteration (cumulative)
+    unsigned epoch;       // fused launches so far
+    unsigned off_m, off_sg, off_h4, off_js, fused_bytes;
 };
 
 struct cslbm_ctx {
@@ -72,7 +78,7 @@ struct cslbm_ops {
     // one time step P[pc],H[hc] -> P[1-pc],H[1-hc] (momentum pass + step
     // pass); force_only: only H[1-hc] from the momentum field jf.  Returns
     // the number of kernels it launched.
-    int (*step)(const cslbm_ctx*, int force_only);
+    int (*step)(cslbm_ctx*, int force_only);
     // P[pc] slots -= F/2 of H[hc] (end of initialisation)
     void (*half_shift)(const cslbm_ctx*);
     // chart change for nodes [v0, v0+cnt): P[pc],H[hc],G[gc] -> P[1-pc],H[1-hc] with G[1-gc]

@@ -7,7 +7,7 @@
 
 #include "ctx.h"
 #include "flat_step.cuh"
-#include "row_step.cuh"
+#include "fused_rows.cuh"
 #include "lbm_device.cuh"
 
 namespace cslbm {
@@ -585,7 +585,7 @@ template <class S, class R> struct Launch {
     {
         launch_momentum<S, R>(c, make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc));
     }
-    static int step(const cslbm_ctx* c, int force_only)
+    static int step(cslbm_ctx* c, int force_only)
     {
         Lat L = make_lat(c);
         if (force_only) {
@@ -594,6 +594,10 @@ template <class S, class R> struct Launch {
             return 1;
         }
         if constexpr (!std::is_same<R, double>::value) {
+            if (c->rows.fused_ok && c->p.step_kernel == CSLBM_STEP_AUTO) {
+                const int k = launch_fused_step<S>(c, L, c->pc, c->hc, c->gc, step_error_flag(c));
+                if (k > 0) return k;
+            }
             if (c->rows.ok) return launch_rows_step<S>(c, L, c->pc, c->hc, c->gc, step_error_flag(c));
         }
         launch_flat_step<S, R>(c, L, P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc));

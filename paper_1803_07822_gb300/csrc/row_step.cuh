@@ -130,7 +130,8 @@ __device__ __forceinline__ int wrap_or(int r, int n, bool periodic, bool& inside
     return r < 0 ? r + n : r - n;
 }
 
-// Tensor maps handed to the pass (grid constants).
+// Tensor maps handed to the pass (grid constants: a copy instruction must
+// name a map in parameter, constant or global memory, never a local copy).
 struct Maps {
     CUtensorMap pop, jf, geo, hist;
 };
@@ -140,10 +141,14 @@ struct Maps {
 // per rho u layer, and for the geometry and the history (24 copies); the
 // first and last tile of a periodic y axis copy row by row, so that the rows
 // across the periodic seam come from the other end of the axis.
+constexpr int PART_MAIN = 1, PART_JF = 2;  // populations + geometry + history / rho u
+
 template <class S>
-__device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const Maps& M, int t, unsigned char* st,
+__device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const CUtensorMap* mpop,
+                                           const CUtensorMap* mjf, const CUtensorMap* mgeo, const CUtensorMap* mhist,
+                                           int t, unsigned char* st,
                                            unsigned long long* bar, const S* __restrict__ Pin,
-                                           const Mom4<float>* __restrict__ jf, int lane)
+                                           const Mom4<float>* __restrict__ jf, int lane, int part, int stride = 32)
 {
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
     const unsigned N = (unsigned)L.N;
@@ -154,7 +159,9 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const M
     const bool seam = yper && (y0 == 0 || y0 + pl.TR >= n1);
     const int npop = seam ? Q * TRe : Q, njf = seam ? 3 * (TRe + 2) : 3;
     const int total = npop + njf + 2;
-    for (int c = lane; c < total; c += 32) {
+    for (int c = lane; c < total; c += stride) {
+        const bool is_jf = c >= npop && c < npop + njf;
+        if (!(part & (is_jf ? PART_JF : PART_MAIN))) continue;
         if (c < npop) {
             const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0;
             bool in = true;
@@ -162,7 +169,7 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const M
             if (!seam) {
                 const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
                 bar_expect_tx(bar, bytes);
-                tensor4(st + (size_t)l * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, l, bar);
+                tensor4(st + (size_t)l * NT * sizeof(S), mpop, 0, y0 - cvec_rt(l, 1), zs, l, bar);
                 continue;
             }
             const int y = y0 + r;
@@ -181,7 +188,11 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const M
             if (!seam) {
                 const unsigned bytes = (unsigned)((pl.TR + 2) * n0 * sizeof(Mom4<float>));
                 bar_expect_tx(bar, bytes);
-                tensor4(dst, &M.jf, 0, 0, y0 - 1, zs, bar);
+                // first line of rows y0 - 1 .. y0 + TR of plane zs (row y0 - 1 of
+                // the first tile reads the previous plane's last row or the
+                // fill: only face rows use it)
+                const int line = (int)(((long long)zs * n1 + y0 - 1) * 4 * n0 / pl.JL);
+                tensor2(dst, mjf, 0, line, bar);
                 continue;
             }
             const int ys = wrap_or(y0 - 1 + b, n1, yper, in);
@@ -191,11 +202,81 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const M
             bulk_copy(dst, jf + ((unsigned)zs * n1 + ys) * n0, bytes, bar);
         } else if (c == npop + njf) {
             bar_expect_tx(bar, NGEO * NT * 4u);
-            tensor2(st + pl.off_geo, &M.geo, (int)v0, 0, bar);
+            tensor2(st + pl.off_geo, mgeo, (int)v0, 0, bar);
         } else {
             bar_expect_tx(bar, NHIST * NT * 4u);
-            tensor2(st + pl.off_hist, &M.hist, (int)v0, 0, bar);
+            tensor2(st + pl.off_hist, mhist, (int)v0, 0, bar);
         }
+    }
+}
+
+// The compute warps' part of a staged tile: every input of the thread's node
+// into registers, the stage handed back to the copy warp (one arrive per
+// warp on `empty`), then the step of the node, stored straight to HBM.
+// Nodes on a face are left to k_step_faces.
+template <class S>
+__device__ __forceinline__ void step_tile(const Lat& L, const Plan& pl, const unsigned char* st, int t, int tid,
+                                          unsigned long long* empty, S* __restrict__ Pout, float* __restrict__ hout)
+{
+    const int n0 = L.n[0], n1 = L.n[1];
+    const unsigned N = (unsigned)L.N;
+    const int r = tid / n0, x = tid - r * n0;
+    const int xm = x == 0 ? n0 - 1 : x - 1, xp = x == n0 - 1 ? 0 : x + 1;
+    const int qb = r * n0, q0 = qb + x, qm = qb + xm, qp = qb + xp;
+    const bool xface = L.bclo[0] != BC_PERIODIC && (x == 0 || x == n0 - 1);
+    const bool yper = L.bclo[1] == BC_PERIODIC;
+    const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
+    const int y = y0 + r;
+    // nodes on a face are stepped by k_step_faces
+    const bool active = r < pl.TR && y < n1 && !(xface || (!yper && (y == 0 || y == n1 - 1)));
+    // every input of the node into registers first, so that the stage
+    // goes back to the copy warp before the arithmetic starts
+    float sv[Q];
+    GeoT<float> G;
+    HistT<float> Hp;
+    float d[9][3];
+    if (active) {
+        const S* pop = reinterpret_cast<const S*>(st);
+        const float* gs = reinterpret_cast<const float*>(st + pl.off_geo);
+        const float* hs = reinterpret_cast<const float*>(st + pl.off_hist);
+        const Mom4<float>* js = reinterpret_cast<const Mom4<float>*>(st + pl.off_jf);
+#pragma unroll
+        for (int l = 0; l < Q; l++) {
+            const int cx = cvec(l, 0);
+            sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
+        }
+        G.sg = gs[q0];
+#pragma unroll
+        for (int a = 0; a < 6; a++) G.gi[a] = gs[(1 + a) * NT + q0];
+#pragma unroll
+        for (int a = 0; a < 18; a++) G.gam[a] = gs[(7 + a) * NT + q0];
+        Hp.A = hs[q0];
+#pragma unroll
+        for (int a = 0; a < 3; a++) Hp.B[a] = hs[(1 + a) * NT + q0];
+#pragma unroll
+        for (int a = 0; a < 6; a++) Hp.C[a] = hs[(4 + a) * NT + q0];
+        // rho u at site (x + cx, y + cy, z + cz): layer cz + 1, row r + 1 + cy
+        const int jb = n0;  // row r + 1 starts at (r + 1) n0 = qb + n0
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+            const int ip = (cz + 1) * pl.JS + cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qp : qm));
+            const int im = (1 - cz) * pl.JS - cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qm : qp));
+            const Mom4<float> p = js[ip], m = js[im];
+            d[k][0] = p.x - m.x;
+            d[k][1] = p.y - m.y;
+            d[k][2] = p.z - m.z;
+        }
+    }
+    __syncwarp();
+    if ((tid & 31) == 0) bar_arrive(empty);
+    if (active) {
+        G.isg = recip(G.sg);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
+        const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
+        step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
     }
 }
 
@@ -231,7 +312,8 @@ __global__ void __launch_bounds__(NTHR, 1)
                 if (!__all_sync(0xffffffffu, ok)) break;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            issue_tile<S>(L, pl, M, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s], Pin, jf, lane);
+            issue_tile<S>(L, pl, &M.pop, &M.jf, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s],
+                          Pin, jf, lane, PART_MAIN | PART_JF);
             __syncwarp();
             if (lane == 0) bar_arrive(&full[s]);
         }
@@ -241,12 +323,6 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!bar_wait(&full[j % STAGES], (j / STAGES) & 1) && lane == 0) atomicOr(err, 2);
     } else {
         // compute warps
-        const unsigned N = (unsigned)L.N;
-        const int r = tid / n0, x = tid - r * n0;
-        const int xm = x == 0 ? n0 - 1 : x - 1, xp = x == n0 - 1 ? 0 : x + 1;
-        const int qb = r * n0, q0 = qb + x, qm = qb + xm, qp = qb + xp;
-        const bool xface = L.bclo[0] != BC_PERIODIC && (x == 0 || x == n0 - 1);
-        const bool yper = L.bclo[1] == BC_PERIODIC;
         int i = 0;
         for (int t = blockIdx.x; t < pl.ntiles; t += gridDim.x, i++) {
             const int s = i % STAGES;
@@ -254,60 +330,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                 atomicOr(err, 4);
                 break;
             }
-            const unsigned char* st = smem_rows + (size_t)s * pl.stage_bytes;
-            const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
-            const int y = y0 + r;
-            // nodes on a face are stepped by k_step_faces
-            const bool active = r < pl.TR && y < n1 && !(xface || (!yper && (y == 0 || y == n1 - 1)));
-            // every input of the node into registers first, so that the stage
-            // goes back to the copy warp before the arithmetic starts
-            float sv[Q];
-            GeoT<float> G;
-            HistT<float> Hp;
-            float d[9][3];
-            if (active) {
-                const S* pop = reinterpret_cast<const S*>(st);
-                const float* gs = reinterpret_cast<const float*>(st + pl.off_geo);
-                const float* hs = reinterpret_cast<const float*>(st + pl.off_hist);
-                const Mom4<float>* js = reinterpret_cast<const Mom4<float>*>(st + pl.off_jf);
-#pragma unroll
-                for (int l = 0; l < Q; l++) {
-                    const int cx = cvec(l, 0);
-                    sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
-                }
-                G.sg = gs[q0];
-#pragma unroll
-                for (int a = 0; a < 6; a++) G.gi[a] = gs[(1 + a) * NT + q0];
-#pragma unroll
-                for (int a = 0; a < 18; a++) G.gam[a] = gs[(7 + a) * NT + q0];
-                Hp.A = hs[q0];
-#pragma unroll
-                for (int a = 0; a < 3; a++) Hp.B[a] = hs[(1 + a) * NT + q0];
-#pragma unroll
-                for (int a = 0; a < 6; a++) Hp.C[a] = hs[(4 + a) * NT + q0];
-                // rho u at site (x + cx, y + cy, z + cz): layer cz + 1, row r + 1 + cy
-                const int jb = n0;  // row r + 1 starts at (r + 1) n0 = qb + n0
-#pragma unroll
-                for (int k = 0; k < 9; k++) {
-                    const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-                    const int ip = (cz + 1) * pl.JS + cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qp : qm));
-                    const int im = (1 - cz) * pl.JS - cy * jb + jb + (cx == 0 ? q0 : (cx > 0 ? qm : qp));
-                    const Mom4<float> p = js[ip], m = js[im];
-                    d[k][0] = p.x - m.x;
-                    d[k][1] = p.y - m.y;
-                    d[k][2] = p.z - m.z;
-                }
-            }
-            __syncwarp();
-            if ((tid & 31) == 0) bar_arrive(&empty[s]);
-            if (active) {
-                G.isg = recip(G.sg);
-#pragma unroll
-                for (int k = 0; k < 3; k++)
-                    G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
-                const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
-                step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
-            }
+            step_tile<S>(L, pl, smem_rows + (size_t)s * pl.stage_bytes, t, tid, &empty[s], Pout, hout);
         }
     }
     __syncthreads();

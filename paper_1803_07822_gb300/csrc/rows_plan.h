@@ -20,6 +20,9 @@ struct Plan {
     int z0;        // first plane that is not a face plane
     int ntiles;    // nyb * (planes that are not face planes)
     int JS;        // nodes per rho u layer: (TR + 2) n0 rounded up to 8
+    int JL;        // floats per line of the 2-D view of rho u: the largest power
+                   // of two <= 256 dividing 4 n0
+    int JR;        // lines of one rho u layer: (TR + 2) 4 n0 / JL
     unsigned off_jf, off_geo, off_hist, stage_bytes;
 };
 
@@ -38,6 +41,9 @@ inline bool make_plan(const int n[3], bool zper, int s_bytes, int max_smem, Plan
     pl.z0 = zper ? 0 : 1;
     pl.ntiles = pl.nyb * (zper ? n[2] : n[2] - 2);
     pl.JS = ((pl.TR + 2) * n[0] + 7) / 8 * 8;
+    pl.JL = 256;
+    while ((4 * n[0]) % pl.JL != 0) pl.JL /= 2;
+    pl.JR = (pl.TR + 2) * 4 * n[0] / pl.JL;
     unsigned o = ((unsigned)(19 * NT * s_bytes) + 127u) & ~127u;
     pl.off_jf = o;
     o += 3u * pl.JS * 16u;
@@ -48,6 +54,20 @@ inline bool make_plan(const int n[3], bool zper, int s_bytes, int max_smem, Plan
     o += NHIST * NT * 4u;
     pl.stage_bytes = (o + 127u) & ~127u;
     return (long long)smem_bytes(pl) <= max_smem;
+}
+
+// smem layout of the fused pass after the two step stages: the momentum
+// stage (populations, sqrt(g), A and B; off_sg and off_h4 relative to it),
+// two rho u tiles of NT nodes, then ten mbarriers; false when it does not fit
+inline bool fused_layout(const Plan& pl, int s_bytes, int max_smem, unsigned& off_m, unsigned& off_sg,
+                         unsigned& off_h4, unsigned& off_js, unsigned& bytes)
+{
+    off_m = 2u * pl.stage_bytes;
+    off_sg = ((unsigned)(19 * NT * s_bytes) + 127u) & ~127u;
+    off_h4 = off_sg + NT * 4u;
+    off_js = off_m + ((off_h4 + 4u * NT * 4u + 127u) & ~127u);
+    bytes = off_js + 2u * NT * 16u + 10u * 8u;
+    return (int)bytes <= max_smem;
 }
 
 }  // namespace rows

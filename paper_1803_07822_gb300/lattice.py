@@ -16,7 +16,7 @@ from . import _abi
 from ._abi import call
 
 STORAGE = {"fp32": _abi.FP32, "fp16": _abi.FP16S, "bf16": _abi.BF16S, "fp64": _abi.FP64}
-STEP_KERNEL = {"auto": _abi.STEP_AUTO, "flat": _abi.STEP_FLAT}
+STEP_KERNEL = {"auto": _abi.STEP_AUTO, "flat": _abi.STEP_FLAT, "rows": _abi.STEP_ROWS}
 
 
 def _torch():
@@ -33,7 +33,8 @@ class CurvedLattice:
     tau: BGK relaxation time; fext: contravariant body-force density;
     storage: "fp32", "fp16", "bf16" (weight-shifted, FP32 arithmetic) or
     "fp64"; literal_a2: transform a_(2) itself on chart changes;
-    step_kernel: "auto" (row-staged pass where it applies) or "flat".
+    step_kernel: "auto" (fused row pass, else row pass, else flat pass),
+    "rows" (row pass with a separate momentum kernel) or "flat".
     """
 
     def __init__(self, n, bc_lo=(0, 0, 0), bc_hi=None, tau=0.8, theta=0.0, fext=(0.0, 0.0, 0.0),

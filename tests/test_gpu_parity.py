@@ -50,9 +50,10 @@ TOL = {"fp64": 1e-11, "fp32": 1e-5}
 
 LAYOUTS = [(2, 0, 1), (0, 1, 2)]  # (wall, span, flow): walls across z / across x
 
-# storage and step pass: FP64 always takes the flat pass; FP32 runs both the
-# row-staged pass (auto, where the shape allows it) and the flat pass
-KERNELS = [("fp64", "auto"), ("fp32", "auto"), ("fp32", "flat")]
+# storage and step pass: FP64 always takes the flat pass; FP32 runs the fused
+# row pass (auto: momentum and step in one launch, where axis 2 is
+# non-periodic), the row pass with a separate momentum kernel, and the flat pass
+KERNELS = [("fp64", "auto"), ("fp32", "auto"), ("fp32", "rows"), ("fp32", "flat")]
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -160,7 +161,7 @@ def test_dynamic_metric_with_transform(literal):
         compare(g, o, ch_old.J9, TOL[storage], storage)
 
 
-@pytest.mark.parametrize("kernel", ["auto", "flat"])
+@pytest.mark.parametrize("kernel", ["auto", "rows", "flat"])
 @pytest.mark.parametrize("storage,tol", [("fp16", 3e-2), ("bf16", 1e-1)])
 def test_reduced_precision_storage_error(storage, tol, kernel):
     """Weight-shifted FP16/BF16 storage with FP32 arithmetic, error vs the
@@ -267,7 +268,7 @@ def tiled_case(n, layout, kind):
                        (layout[0], 1): smooth_wall_velocity(n, layout)})
 
 
-@pytest.mark.parametrize("kernel", ["auto", "flat"])
+@pytest.mark.parametrize("kernel", ["auto", "rows", "flat"])
 @pytest.mark.parametrize("name,n,layout,kind", TILED, ids=[t[0] for t in TILED])
 def test_tiled_fp32(name, n, layout, kind, kernel):
     rng = np.random.default_rng(11)
@@ -284,12 +285,14 @@ def test_tiled_fp32(name, n, layout, kind, kernel):
     compare(g, o, w["chart"].J9, TOL["fp32"], name)
 
 
+@pytest.mark.parametrize("kernel", ["auto", "rows"])
 @pytest.mark.parametrize("name,n,layout,kind", TILED[:3], ids=[t[0] for t in TILED[:3]])
-def test_row_staged_and_flat_passes_agree(name, n, layout, kind):
-    """The two step passes compute the same arithmetic in the same order per
-    node; after 50 steps they agree to FP32 rounding."""
+def test_row_staged_and_flat_passes_agree(name, n, layout, kind, kernel):
+    """The step passes compute the same arithmetic per node (the fused pass
+    forms rho u of face nodes in closed form from their inner nodes); after
+    50 steps they agree to FP32 rounding."""
     w = tiled_case(n, layout, kind)
-    a, _ = make_pair(w, "fp32", step_kernel="auto")
+    a, _ = make_pair(w, "fp32", step_kernel=kernel)
     b, _ = make_pair(w, "fp32", step_kernel="flat")
     a.init_equilibrium()
     b.init_equilibrium()
