@@ -228,6 +228,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--snapshots", type=int, default=3)
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
+    ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16", "fp64"],
+                    help="storage of the populations (default: the workload's, FP32)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -240,6 +242,11 @@ def main():
 
     rank, world, local = dist_setup(args)
     spec = workload_spec(args.workload)
+    if args.storage:
+        spec["storage"] = args.storage
+        spec["label"] = spec["label"].replace(
+            "FP32", args.storage.upper() + (" weight-shifted storage, FP32 arithmetic" if args.storage in ("fp16", "bf16")
+                                            else " storage"))
     w = I.dynamic_channel(n=spec["n"], seed=spec["seed"] + rank, n_modes=spec["n_modes"], amp=spec["amp"],
                           tau=spec["tau"], re=spec["re"])
     N = int(np.prod(spec["n"]))
