@@ -200,6 +200,93 @@ def oracle_cycle_sample(spec, steps, warm):
     return N * STEPS_PER_CYCLE * steps / t_total / 1e6, t_total, n, cores
 
 
+def bench_batch(args):
+    """The batched form: 64 independent periodic channels with sides drawn from
+    U{32..96} per axis, 4-mode deformations of 2-10 % amplitude, tau in
+    [0.55, 1.0], FP32, all advanced by two launches per LBM step replayed from
+    a CUDA graph, block size from the library's autotuner.  A bench step is 10
+    LBM steps of every channel.  Also timed: the same channels stepped one
+    channel at a time (each its own launches), the per-channel baseline."""
+    import torch
+
+    from paper_1803_07822_gb300.lattice import CurvedBatch
+    rank, world, local = dist_setup(args)
+    ws = I.batch_channels(nb=64, seed0=4000 + 1000 * rank)
+    b = CurvedBatch([dict(n=w["n"], bc_lo=w["bc_lo"], bc_hi=w["bc_hi"], tau=w["tau"], fext=w["fext"]) for w in ws])
+    for i, w in enumerate(ws):
+        b[i].set_chart(w["chart"])
+        b[i].init_equilibrium()
+    tb, tune_ms = b.tune(reps=5)
+    stream = b.stream
+    N = b.nodes
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        b.step(STEPS_PER_CYCLE)
+    l0 = b.launches()
+    clocks = Clocks(local)
+    ms = timed(lambda: b.step(STEPS_PER_CYCLE), args.steps)
+    clk = clocks.stop()
+    launches = b.launches() - l0
+    ms = reduce_max(ms, world)
+
+    def per_channel():
+        for c in b:
+            c.step(STEPS_PER_CYCLE)
+
+    kpc = max(1, args.steps // 3)
+    per_channel()
+    ms_pc = reduce_max(timed(per_channel, kpc), world) / kpc
+    bad = [i for i, c in enumerate(b) if not c.check()]
+    # end to end: the same steps with the 64 channel masses read back to the host every bench step
+    t0 = time.perf_counter()
+    for _ in range(kpc):
+        b.step(STEPS_PER_CYCLE)
+        masses = [c.total_mass() for c in b]
+    e2e_s = (time.perf_counter() - t0) / kpc
+    peak, peak_kind = peaks()
+    steps_total = STEPS_PER_CYCLE * args.steps
+    value = world * N * steps_total / (ms * 1e-3) / 1e6
+    ach = BYTES_PER_NODE["fp32"] * N * steps_total / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "64 independent deformed periodic channels, sides U{32..96}, 4 modes 2-10 %, "
+                               "tau U[0.55, 1.0], FP32, batched (one momentum + one step launch per LBM step, "
+                               "CUDA graph)", "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
+                   "l2": "inputs > L2 (1.4 GB of state per LBM step), no flush", "block_nodes": tb,
+                   "tune_ms_per_lbm_step": tune_ms, "state_finite_after_run": not bad, "unstable_channels": bad},
+        "per_channel_launches": {"value": world * N * STEPS_PER_CYCLE / (ms_pc * 1e-3) / 1e6, "unit": UNIT,
+                                 "ms_per_step": ms_pc},
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "one batched LBM step: k_batch_momentum + k_batch_step", "bytes_per_node": 332},
+        "e2e": {"value": world * N * STEPS_PER_CYCLE / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * len(masses)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -223,7 +310,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
-    ap.add_argument("--workload", default="dynamic", choices=["dynamic", "target256", "crop64"])
+    ap.add_argument("--workload", default="dynamic", choices=["dynamic", "target256", "crop64", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--snapshots", type=int, default=3)
@@ -235,6 +322,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return bench_batch(args)
 
     import torch
 

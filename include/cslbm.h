@@ -188,6 +188,42 @@ cslbm_status cslbm_profile_read(cslbm_ctx* ctx, double* step_ms, long long* nste
 cslbm_status cslbm_total_mass_static(cslbm_ctx* ctx, double* out);
 
 /* Message of the last failure on this thread ("" if none). */
+/* ---------------------------------------------------------------------------
+ * Batched form: nb independent channels (each its own cslbm_params, FP32
+ * storage, any sizes) advanced together.  Each channel is an ordinary
+ * context, reachable with cslbm_batch_context, on which every call above
+ * works (geometry, boundary velocities, initialisation, moments, mass, wall
+ * force, state); its own cslbm_step takes the flat gather pass.
+ * ------------------------------------------------------------------------- */
+typedef struct cslbm_batch cslbm_batch;
+
+/* Device workspace bytes of a batch of nb channels with parameters p[0..nb). */
+cslbm_status cslbm_batch_workspace_bytes(int nb, const cslbm_params* p, size_t* bytes);
+
+/* Create the batch in a caller-owned, 256-byte aligned device workspace; the
+ * channels' contexts use `stream`, the batch steps run on a stream of its own
+ * ordered after and before `stream` with events.  EINVAL for a channel that
+ * is not FP32 or for invalid parameters, ENOMEM for a short workspace. */
+cslbm_status cslbm_batch_create(int nb, const cslbm_params* p, void* workspace, size_t bytes, void* stream,
+                                cslbm_batch** out);
+cslbm_status cslbm_batch_context(cslbm_batch* b, int i, cslbm_ctx** out);
+
+/* nsteps time steps of every channel (Sec. II, Eqs. collision and streaming,
+ * per channel): two launches per step (momentum pass and step pass over all
+ * channels' nodes), replayed two steps at a time from a CUDA graph.
+ * Asynchronous; ESTATE when a channel has no state. */
+cslbm_status cslbm_batch_step(cslbm_batch* b, int nsteps);
+
+/* Autotuner: times the nodes-per-block candidates (128, 256, 512) on this
+ * batch, reps repetitions of one step from the current state each (the state
+ * does not advance), keeps the fastest and returns it in *block_nodes and
+ * the per-step times in ms[3] (either may be null).  Synchronises. */
+cslbm_status cslbm_batch_tune(cslbm_batch* b, int reps, int* block_nodes, float* ms);
+
+/* Kernels launched by cslbm_batch_step so far (graph replays included). */
+cslbm_status cslbm_batch_launches(const cslbm_batch* b, long long* launches);
+cslbm_status cslbm_batch_destroy(cslbm_batch* b);
+
 const char* cslbm_last_error(void);
 
 #ifdef __cplusplus

@@ -58,6 +58,13 @@ SIGNATURES = {
     "cslbm_load_state": [_P, _P, _SZ, _I],
     "cslbm_profile_enable": [_P, _I],
     "cslbm_profile_read": [_P, _D, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+    "cslbm_batch_workspace_bytes": [_I, ctypes.POINTER(Params), ctypes.POINTER(_SZ)],
+    "cslbm_batch_create": [_I, ctypes.POINTER(Params), _P, _SZ, _P, ctypes.POINTER(_P)],
+    "cslbm_batch_context": [_P, _I, ctypes.POINTER(_P)],
+    "cslbm_batch_step": [_P, _I],
+    "cslbm_batch_tune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)],
+    "cslbm_batch_launches": [_P, ctypes.POINTER(ctypes.c_longlong)],
+    "cslbm_batch_destroy": [_P],
     "cslbm_last_error": [],
 }
 

@@ -81,14 +81,13 @@ __device__ __forceinline__ bool flat_node(const Lat& L, int& x, int& y, int& z, 
     return true;
 }
 
+// rho u of one node into jf[v] (pull gather; boundary rule on face nodes)
 template <class S, class R>
-__global__ void __launch_bounds__(TB) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                      const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
+__device__ __forceinline__ void momentum_node(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                              const R* __restrict__ geo, Mom4<R>* __restrict__ jf, int x, int y,
+                                              int z, unsigned v)
 {
     const unsigned N = (unsigned)L.N;
-    int x, y, z;
-    unsigned v;
-    if (!flat_node(L, x, y, z, v)) return;
     if (on_boundary(L, x, y, z)) {
         momentum_boundary<S, R>(L, P, hist, geo, x, y, z, jf);
         return;
@@ -109,6 +108,16 @@ __global__ void __launch_bounds__(TB) k_momentum_flat(Lat L, const S* __restrict
     j.z = fmad(sg, m1[2], R(0.5) * __ldg(hist + 3 * N + v));
     j.w = R(0);
     jf[v] = j;
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TB) k_momentum_flat(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                      const R* __restrict__ geo, Mom4<R>* __restrict__ jf)
+{
+    int x, y, z;
+    unsigned v;
+    if (!flat_node(L, x, y, z, v)) return;
+    momentum_node<S, R>(L, P, hist, geo, jf, x, y, z, v);
 }
 
 // rho u at a stencil site that may lie one step outside a non-periodic face:
@@ -239,15 +248,15 @@ __device__ __noinline__ void step_boundary(const Lat& L, const S* __restrict__ P
     step_boundary_body<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
 }
 
+// the step of one node: pull gather, moments, gradient from the rho u field,
+// forcing, collision, store (the boundary rule and ghost stencil out of line
+// on face nodes)
 template <class S, class R>
-__global__ void __launch_bounds__(TB, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
-                                                     const R* __restrict__ hin, R* __restrict__ hout,
-                                                     const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+__device__ __forceinline__ void step_node(const Lat& L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                          const R* __restrict__ hin, R* __restrict__ hout, const R* __restrict__ geo,
+                                          const Mom4<R>* __restrict__ jf, int x, int y, int z, unsigned v)
 {
     const unsigned N = (unsigned)L.N;
-    int x, y, z;
-    unsigned v;
-    if (!flat_node(L, x, y, z, v)) return;
     if (on_boundary(L, x, y, z)) {
         step_boundary<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
         return;
@@ -271,6 +280,17 @@ __global__ void __launch_bounds__(TB, 2) k_step_flat(Lat L, const S* __restrict_
         d[k][2] = p.z - m.z;
     }
     step_core<S, R>(L, s, G, Hp, d, Pout, hout, v, N);
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TB, 2) k_step_flat(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                     const R* __restrict__ hin, R* __restrict__ hout,
+                                                     const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
+{
+    int x, y, z;
+    unsigned v;
+    if (!flat_node(L, x, y, z, v)) return;
+    step_node<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z, v);
 }
 
 // The nodes on non-periodic faces as up to six boxes without overlap: the

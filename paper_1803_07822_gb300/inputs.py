@@ -248,14 +248,14 @@ def _bcs(layout, flow_rule_lo, flow_rule_hi):
     return tuple(lo), tuple(hi)
 
 
-def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None, layout=LAYOUT):
+def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None, layout=LAYOUT, kmax=4, lmax=3):
     """Walls across the wall axis, periodic span and flow, body-force drive
     along the flow axis with centre-line speed umax."""
     nu = (tau - 0.5) / 3.0
     w, _, a_s = layout
     H = n[w] - 1
-    dfm = fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, modes=modes, coeffs=coeffs,
-                              layout=layout)
+    dfm = fourier_deformation(n, n_modes, amp, seed, flow_periodic=True, kmax=kmax, lmax=lmax, modes=modes,
+                              coeffs=coeffs, layout=layout)
     lo, hi = _bcs(layout, PERIODIC, PERIODIC)
     fext = [0.0, 0.0, 0.0]
     fext[a_s] = body_force(nu, umax, H)
@@ -297,3 +297,38 @@ def dynamic_channel_at(w, t):
     faces = {(lay[2], 0): inflow_profile(w["n"], chart, w["umax"], lay),
              (lay[0], 1): wall_velocity(w["n"], chart, w["base"].scaled(adot), lay)}
     return chart, faces
+
+
+def max_slope(dfm):
+    """Largest wall slope |grad d| of a deformation over the nodes."""
+    return float(np.sqrt(dfm.dp ** 2 + dfm.ds ** 2).max())
+
+
+def batch_channels(nb=64, seed0=4000, side=(32, 96), n_modes=4, amp=(0.02, 0.10), tau=(0.55, 1.0), umax=0.05,
+                   layout=LAYOUT, kmax=2, lmax=1, slope_cap=0.25):
+    """Independent periodic channels of uneven sizes (walls across the wall
+    axis, periodic span and flow, body-force drive with centre-line speed
+    umax): channel i draws its three sides from U{side[0]..side[1]}, its
+    deformation amplitude (fraction of the height) from U[amp], tau from
+    U[tau] with numpy.random.default_rng(seed0 + i + 100000), and its
+    n_modes-mode deformation (wavenumbers up to kmax along the flow, lmax
+    across) with seed seed0 + i.  A deformation whose largest wall slope
+    exceeds slope_cap is scaled down to it: the second-order method on a
+    single-mode channel is stable up to a slope of about 0.3 at tau = 0.6 (and
+    0.5 at tau = 0.9), and a height-relative amplitude on a channel taller
+    than it is long gives steeper walls than that.  The amplitude a channel
+    ends with is its 'amp_eff'."""
+    out = []
+    for i in range(nb):
+        rng = np.random.default_rng(seed0 + i + 100000)
+        n = tuple(int(v) for v in rng.integers(side[0], side[1] + 1, size=3))
+        a = float(rng.uniform(*amp))
+        t = float(rng.uniform(*tau))
+        w = periodic_channel(n, t, umax, n_modes, a, seed0 + i, layout=layout, kmax=kmax, lmax=lmax)
+        s = max_slope(w["dfm"])
+        if slope_cap is not None and s > slope_cap:
+            a *= slope_cap / s
+            w = periodic_channel(n, t, umax, n_modes, a, seed0 + i, layout=layout, kmax=kmax, lmax=lmax)
+        w["amp_eff"] = a
+        out.append(w)
+    return out

@@ -185,9 +185,96 @@ class CurvedLattice:
         return ms.value, n.value, k.value
 
     def close(self):
-        if getattr(self, "ctx", None) is not None and self.ctx.value:
+        if getattr(self, "_owned", True) and getattr(self, "ctx", None) is not None and self.ctx.value:
             _abi.load().cslbm_destroy(self.ctx)
-            self.ctx = ctypes.c_void_p()
+        self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @classmethod
+    def _channel(cls, ctx, n, device, stream, owner):
+        """A view of a context owned by a batch (not destroyed by this object)."""
+        self = cls.__new__(cls)
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        self.device = device
+        self.stream = stream
+        self.ctx = ctx
+        self._owned = False
+        self._owner = owner
+        return self
+
+
+def _params(n, bc_lo, bc_hi, tau, theta, fext, storage, literal_a2, step_kernel):
+    return _abi.Params((ctypes.c_int * 3)(*n), (ctypes.c_int * 3)(*bc_lo), (ctypes.c_int * 3)(*bc_hi), float(tau),
+                       float(theta), (ctypes.c_double * 3)(*fext), STORAGE[storage], int(bool(literal_a2)),
+                       STEP_KERNEL[step_kernel])
+
+
+class CurvedBatch:
+    """Independent FP32 channels of any sizes advanced together (two kernel
+    launches per step for the whole batch, replayed from a CUDA graph).
+
+    channels: list of dicts with keys n, bc_lo, bc_hi, tau and optionally
+    fext, theta.  batch[i] is a CurvedLattice view of channel i (geometry,
+    boundary velocities, initialisation, moments, forces work on it)."""
+
+    def __init__(self, channels, device=None, stream=None):
+        torch = _torch()
+        _abi.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        nb = len(channels)
+        arr = (_abi.Params * nb)()
+        for i, ch in enumerate(channels):
+            bc_hi = ch.get("bc_hi", ch["bc_lo"])
+            arr[i] = _params(ch["n"], ch["bc_lo"], bc_hi, ch["tau"], ch.get("theta", 0.0),
+                             ch.get("fext", (0.0, 0.0, 0.0)), "fp32", False, "flat")
+        nbytes = ctypes.c_size_t(0)
+        call("cslbm_batch_workspace_bytes", nb, arr, ctypes.byref(nbytes))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self.batch = ctypes.c_void_p()
+        call("cslbm_batch_create", nb, arr, self.workspace.data_ptr(), nbytes.value, self.stream.cuda_stream,
+             ctypes.byref(self.batch))
+        self.channels = []
+        for i, ch in enumerate(channels):
+            c = ctypes.c_void_p()
+            call("cslbm_batch_context", self.batch, i, ctypes.byref(c))
+            self.channels.append(CurvedLattice._channel(c, ch["n"], self.device, self.stream, self))
+        self.nodes = sum(c.N for c in self.channels)
+
+    def __len__(self):
+        return len(self.channels)
+
+    def __getitem__(self, i):
+        return self.channels[i]
+
+    def step(self, nsteps=1):
+        call("cslbm_batch_step", self.batch, int(nsteps))
+
+    def tune(self, reps=10):
+        """Pick the nodes per block by timing the candidates on this batch;
+        returns (chosen, {candidate: ms per step})."""
+        tb = ctypes.c_int(0)
+        ms = (ctypes.c_float * 3)()
+        call("cslbm_batch_tune", self.batch, int(reps), ctypes.byref(tb), ms)
+        return tb.value, {128: ms[0], 256: ms[1], 512: ms[2]}
+
+    def launches(self):
+        k = ctypes.c_longlong(0)
+        call("cslbm_batch_launches", self.batch, ctypes.byref(k))
+        return k.value
+
+    def close(self):
+        if getattr(self, "batch", None) is not None and self.batch.value:
+            for c in self.channels:
+                c.ctx = ctypes.c_void_p()
+            _abi.load().cslbm_batch_destroy(self.batch)
+            self.batch = ctypes.c_void_p()
 
     def __del__(self):
         try:
