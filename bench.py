@@ -44,11 +44,13 @@ STEPS_PER_CYCLE = 10
 BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 + 80 + 100,
                   "bf16": 19 * 2 * 2 + 80 + 100, "fp64": 19 * 8 * 2 + 80 + 100}
 # DRAM bytes per node update (dram__bytes_read.sum + dram__bytes_write.sum of
-# k_momentum_flat + k_step_flat) from one ncu capture of the 64x128x64 crop of
-# the same channel, FP32 storage; both passes touch every node once, so the
-# per-launch traffic scales with the node count.  Only valid for the kernels
-# as they were captured.
-MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
+# the kernels of one LBM step, per launch, divided by the nodes) from ncu
+# launch lists: the flat pass on the 64x128x64 crop of the same channel (both
+# of its passes touch every node once, so the bytes scale with the nodes);
+# the fused pass (k_step_fused + k_step_faces) on the 128x128x256 channel
+# itself.  FP32 storage; only valid for the kernels as they were captured.
+MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288,
+                                ("fused", "fp32"): (1715320015.2 + 32559662.5) / 4194304}
 
 
 def step_pass(n, storage, step_kernel, axis2_periodic=False):
