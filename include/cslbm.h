@@ -189,6 +189,51 @@ cslbm_status cslbm_total_mass_static(cslbm_ctx* ctx, double* out);
 
 /* Message of the last failure on this thread ("" if none). */
 /* ---------------------------------------------------------------------------
+ * Adjoint: gradients of a wall force with respect to the geometry (FP32 or
+ * FP64 storage; periodic faces and walls at rest; static metric; state
+ * initialised at rest with cslbm_init_equilibrium(ctx, NULL, NULL, ...)).
+ * The caller keeps the forward states (checkpoints) and walks back in time:
+ *   attach -> (forward: init, steps, the final state in the context)
+ *   seed_wall_force -> for t = T-1 .. 0 { load state(t); step_backward }
+ *   -> init_backward -> metric_grad.
+ * All device pointers; asynchronous on the context's stream.
+ * ------------------------------------------------------------------------- */
+
+/* Device workspace bytes of the adjoint fields of a context (EINVAL for
+ * FP16/BF16 storage or inflow/outflow faces). */
+cslbm_status cslbm_adjoint_workspace_bytes(const cslbm_ctx* ctx, size_t* bytes);
+
+/* Attach a caller-owned, 256-byte aligned workspace for the adjoint fields
+ * (zeroed). */
+cslbm_status cslbm_adjoint_attach(cslbm_ctx* ctx, void* workspace, size_t bytes);
+
+/* Objective e3 . F, F the force of the fluid on the wall (axis, side) as
+ * cslbm_wall_force computes it from the context's current state (the state
+ * after the last forward step; Sec. III, momentum exchange on the wall
+ * nodes): sets the adjoint of the state to dJ/dstate and the geometry and
+ * Jacobian adjoints to dJ/dgeometry, dJ/dJ. */
+cslbm_status cslbm_adjoint_seed_wall_force(cslbm_ctx* ctx, int axis, int side, const double e3[3]);
+
+/* The adjoint of one LBM step (Sec. II, Eqs. collision and streaming, with
+ * the forcing of Eqs. forcing-A/B/C and the lattice gradient of App. D): the
+ * context's state must be the state before the step; the adjoint state moves
+ * from after the step to before it and the step's geometry derivatives are
+ * added. */
+cslbm_status cslbm_step_backward(cslbm_ctx* ctx);
+
+/* The adjoint of the rest initialisation (f = f^eq(rho = 1, u = 0), the
+ * history F(-1) := F(0)): adds its geometry derivatives. */
+cslbm_status cslbm_adjoint_init_backward(cslbm_ctx* ctx);
+
+/* The accumulated geometry adjoint through the metric kernel (App. A: g^-1,
+ * sqrt(g), Christoffel symbols from g and dg): FP64 gradients of the
+ * objective with respect to g6 [6][N] and dg18 [18][N] (the inputs of
+ * cslbm_set_metric, passed again), and with respect to the Jacobian J9
+ * [9][N] (grad_J9 may be null). */
+cslbm_status cslbm_adjoint_metric_grad(cslbm_ctx* ctx, const double* g6, const double* dg18, double* grad_g6,
+                                       double* grad_dg18, double* grad_J9);
+
+/* ---------------------------------------------------------------------------
  * Batched form: nb independent channels (each its own cslbm_params, FP32
  * storage, any sizes) advanced together.  Each channel is an ordinary
  * context, reachable with cslbm_batch_context, on which every call above

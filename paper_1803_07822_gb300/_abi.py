@@ -58,6 +58,12 @@ SIGNATURES = {
     "cslbm_load_state": [_P, _P, _SZ, _I],
     "cslbm_profile_enable": [_P, _I],
     "cslbm_profile_read": [_P, _D, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+    "cslbm_adjoint_workspace_bytes": [_P, ctypes.POINTER(_SZ)],
+    "cslbm_adjoint_attach": [_P, _P, _SZ],
+    "cslbm_adjoint_seed_wall_force": [_P, _I, _I, _D],
+    "cslbm_step_backward": [_P],
+    "cslbm_adjoint_init_backward": [_P],
+    "cslbm_adjoint_metric_grad": [_P, _P, _P, _P, _P, _P],
     "cslbm_batch_workspace_bytes": [_I, ctypes.POINTER(Params), ctypes.POINTER(_SZ)],
     "cslbm_batch_create": [_I, ctypes.POINTER(Params), _P, _SZ, _P, ctypes.POINTER(_P)],
     "cslbm_batch_context": [_P, _I, ctypes.POINTER(_P)],

@@ -57,6 +57,10 @@ struct cslbm_ctx {
     const cslbm_ops* ops;
     // profiling
     cslbm_rows rows;
+    struct {
+        void* ws;  // adjoint fields (cslbm_adjoint_attach), or null
+        int lp;    // which of the two adjoint buffers holds the current adjoint state
+    } adj;
     int prof;
     std::vector<cudaEvent_t> ev;  // start/stop pairs of profiled steps
     long long prof_steps;
