@@ -99,19 +99,36 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling of SM clocks and throttle reasons (every 50 ms,
+    timestamped), started before the warm-up; stop() keeps the samples taken
+    between mark_start() and mark_end(), or the one nearest that window when
+    it is shorter than the sampling interval."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+
+    def wait_first(self, limit_s=5.0):
+        t = time.time()
+        while self.p is not None and time.time() - t < limit_s:
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.02)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.p is None:
@@ -121,21 +138,28 @@ class Clocks:
         self.f.flush()
         rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        samples = []
         for r in rows:
             try:
-                sm.append(float(r[0]))
-                mx = max(mx, float(r[1]))
+                ts = r[0].strip()
+                t = time.mktime(time.strptime(ts.split(".")[0], "%Y/%m/%d %H:%M:%S")) + float("0." + ts.split(".")[1])
+                samples.append((t, float(r[1]), float(r[2]),
+                                {name for k, name in enumerate(names) if len(r) > 4 + k and r[4 + k].strip() == "Active"}))
             except (ValueError, IndexError):
                 continue
-            for k, name in enumerate(names):
-                if len(r) > 3 + k and r[3 + k].strip() == "Active":
-                    reasons.add(name)
-        if not sm:
+        if not samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [x for x in samples if self.t0 is not None and self.t0 <= x[0] <= (self.t1 or x[0])]
+        window = "timed region"
+        if not inside:
+            mid = 0.5 * ((self.t0 or 0.0) + (self.t1 or self.t0 or 0.0))
+            inside = [min(samples, key=lambda x: abs(x[0] - mid))]
+            window = "nearest sample to a timed region shorter than the 50 ms interval"
+        reasons = set().union(*[x[3] for x in inside])
+        return {"sm_mhz": statistics.median(x[1] for x in inside), "sm_max_mhz": max(x[2] for x in samples),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "sm_mhz_min": min(x[1] for x in inside)}
 
 
 def dist_setup(args):
@@ -236,11 +260,14 @@ def bench_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    clocks = Clocks(local)
     for _ in range(args.warmup):
         b.step(STEPS_PER_CYCLE)
+    clocks.wait_first()
     l0 = b.launches()
-    clocks = Clocks(local)
+    clocks.mark_start()
     ms = timed(lambda: b.step(STEPS_PER_CYCLE), args.steps)
+    clocks.mark_end()
     clk = clocks.stop()
     launches = b.launches() - l0
     ms = reduce_max(ms, world)
@@ -289,6 +316,91 @@ def bench_batch(args):
         dist.destroy_process_group()
 
 
+ADJOINT_STEPS, ADJOINT_EVERY = 200, 20
+
+
+def adjoint_report(step_kernel):
+    """Adjoint/forward step-time ratio on the adjoint-form channel
+    (inputs.adjoint_channel: 64 x 128 x 64, 32 deformation coefficients,
+    tau 0.8, FP32 storage): the gradient of the streamwise force on the
+    deformed wall after 200 steps from rest with respect to the metric inputs
+    (g, dg, J), through the library's adjoint with checkpoints every 20 steps.
+    backward_ms_per_step is that gradient's device time (CUDA events) over the
+    200 steps: every step recomputed from its checkpoint, its state reloaded
+    and reversed, plus the seed, the rest initialisation and the metric
+    kernel reversed.  forward_ms_per_step is the plain FP32 step of the same
+    lattice.  The chain rule from (g, dg, J) to the coefficients is the
+    caller's torch code and is timed apart.  Accuracy: three coefficient
+    derivatives against central differences (h = 1e-4) of the FP64 forward."""
+    import torch
+
+    from paper_1803_07822_gb300.adjoint import chart_from_coeffs, wall_force_objective
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+    w = I.adjoint_channel()
+    axis = w["layout"][0]
+    e3 = [0.0, 0.0, 0.0]
+    e3[w["layout"][2]] = 1.0
+    lat = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage="fp32",
+                        step_kernel=step_kernel)
+    c = torch.tensor(w["c"], dtype=torch.float64, device="cuda", requires_grad=True)
+    chart = chart_from_coeffs(c, w["n"], w["modes"], w["scale"])
+    leaves = [t.detach().requires_grad_(True) for t in chart]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    for rep in range(2):  # the first pass allocates the adjoint workspace and the checkpoints
+        torch.cuda.synchronize()
+        ev[0].record()
+        J = wall_force_objective(lat, *leaves, ADJOINT_STEPS, ADJOINT_EVERY, axis=axis, side=1, e3=e3)
+        ev[1].record()
+        grads = torch.autograd.grad(J, leaves)
+        ev[2].record()
+        torch.cuda.synchronize()
+    lat.init_equilibrium()
+    ev[3].record()
+    lat.step(ADJOINT_STEPS)
+    ev[4].record()
+    torch.autograd.backward(chart, grads, retain_graph=True)  # first call: lazy initialisation in torch
+    c.grad = None
+    torch.cuda.synchronize()
+    ev[5].record()
+    torch.autograd.backward(chart, grads)
+    ev[6].record()
+    torch.cuda.synchronize()
+    fwd = ev[3].elapsed_time(ev[4]) / ADJOINT_STEPS
+    bwd = ev[1].elapsed_time(ev[2]) / ADJOINT_STEPS
+    sb = lat.state_bytes()
+    mem = lat._adjoint.workspace.numel() + (ADJOINT_STEPS // ADJOINT_EVERY + 1 + ADJOINT_EVERY) * sb
+    g = c.grad.cpu().numpy()
+
+    f64 = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage="fp64",
+                        step_kernel="flat")
+
+    def objective(cv):
+        g6, dg18, J9 = chart_from_coeffs(torch.tensor(cv, dtype=torch.float64, device="cuda"), w["n"], w["modes"],
+                                         w["scale"])
+        f64.set_metric(g6, dg18)
+        f64.set_jacobian(J9)
+        f64.init_equilibrium()
+        f64.step(ADJOINT_STEPS)
+        return float(np.dot(e3, f64.wall_force(axis, 1)))
+
+    picks, h, fd = [0, 9, 27], 1e-4, []
+    for m in picks:
+        cp, cm = w["c"].copy(), w["c"].copy()
+        cp[m] += h
+        cm[m] -= h
+        fd.append((objective(cp) - objective(cm)) / (2 * h))
+    err = float(np.linalg.norm(g[picks] - np.array(fd)) / np.linalg.norm(fd))
+    for x in (lat, f64):
+        x.close()
+    return {"workload": "adjoint-form channel 64x128x64 (span, flow, wall), 32 coefficients, tau 0.8, FP32 storage; "
+                        f"objective: streamwise force on the deformed wall after {ADJOINT_STEPS} steps from rest",
+            "ratio": bwd / fwd, "forward_ms_per_step": fwd, "backward_ms_per_step": bwd,
+            "forward_kernel": step_kernel, "checkpoint_every": ADJOINT_EVERY,
+            "chart_backward_ms": ev[5].elapsed_time(ev[6]),
+            "memory_bytes": mem, "state_bytes": sb,
+            "grad_rel_err_vs_fp64_fd": err, "fd": "central, h = 1e-4, coefficients 0, 9, 27, FP64 GPU forward"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -315,6 +427,7 @@ def main():
     ap.add_argument("--workload", default="dynamic", choices=["dynamic", "target256", "crop64", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward step-time ratio")
     ap.add_argument("--snapshots", type=int, default=3)
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16", "fp64"],
@@ -366,12 +479,14 @@ def main():
         lat.total_mass()
         lat.wall_force(0, 1)
 
+    clocks = Clocks(local)
     for k in range(args.warmup):
         cycle_dev(k)
+    clocks.wait_first()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    clocks = Clocks(local)
+    clocks.mark_start()
     lat.profile(True)
     stream = lat.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -380,6 +495,7 @@ def main():
         cycle_dev(args.warmup + k)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier(world)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -414,6 +530,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, secs, n, cores = oracle_cycle_sample(spec, 2, 0)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -20,14 +20,7 @@ import numpy as np
 
 from . import _abi
 from ._abi import call
-from .inputs import LAYOUT, SYM, grid
-
-
-def fourier_modes(kmax, lmax, kmin=1):
-    """The (k, l) pairs k in kmin..kmax along the flow, l in 0..lmax across,
-    phase 0 (the adjoint-form deformation: one coefficient per pair)."""
-    k, l = np.meshgrid(np.arange(kmin, kmax + 1), np.arange(0, lmax + 1), indexing="ij")
-    return k.ravel().astype(float), l.ravel().astype(float), np.zeros(k.size)
+from .inputs import LAYOUT, SYM, fourier_modes, grid  # noqa: F401  (fourier_modes: the modes of chart_from_coeffs)
 
 
 def chart_from_coeffs(coeffs, n, modes, scale, layout=LAYOUT):
@@ -73,11 +66,12 @@ def chart_from_coeffs(coeffs, n, modes, scale, layout=LAYOUT):
     put(a_p, a_p, xw * dpp / H)
     put(a_p, a_s, xw * dps / H)
     put(a_s, a_s, xw * dss / H)
+    # g_ij = sum_a J^a_i J^a_j and d_k g_ij = sum_a (H^a_ki J^a_j + J^a_i H^a_kj), written out as
+    # elementwise products (a batched 3 x 3 contraction per node is no GEMM)
     Hess = torch.stack([torch.stack([torch.stack(Hs[a][j]) for j in range(3)]) for a in range(3)])  # [a, j, k, N]
-    g = torch.einsum("ain,ajn->ijn", J, J)
-    dg = torch.einsum("akin,ajn->kijn", Hess, J) + torch.einsum("ain,akjn->kijn", J, Hess)
-    g6 = torch.stack([g[i, j] for i, j in SYM])
-    dg18 = torch.stack([dg[kk, i, j] for kk in range(3) for i, j in SYM])
+    g6 = torch.stack([(J[:, i] * J[:, j]).sum(0) for i, j in SYM])
+    dg18 = torch.stack([(Hess[:, kk, i] * J[:, j] + J[:, i] * Hess[:, kk, j]).sum(0)
+                        for kk in range(3) for i, j in SYM])
     return g6, dg18, J.reshape(9, N)
 
 

@@ -59,8 +59,9 @@ __device__ __forceinline__ void node_xyz(const Lat& L, long long v, int& x, int&
 // ghost extrapolation of a stencil site reversed: the adjoint lj of the
 // site's rho u distributed onto the real nodes it was built from
 template <class R>
-__device__ __forceinline__ void site_reverse(const Lat& L, int x, int y, int z, const R lj[3], R* lJF)
+__device__ __noinline__ void site_reverse(const Lat& L, int x, int y, int z, R lj0, R lj1, R lj2, R* lJF)
 {
+    const R lj[3] = {lj0, lj1, lj2};
     int x0, x1, y0, y1, z0, z1;
     float wx0, wx1, wy0, wy1, wz0, wz1;
     site_axis(x, L.n[0], L.bclo[0] == BC_PERIODIC, L.bchi[0] == BC_PERIODIC, x0, x1, wx0, wx1);
@@ -79,7 +80,7 @@ __device__ __forceinline__ void site_reverse(const Lat& L, int x, int y, int z, 
 
 // pass A
 template <class R>
-__global__ void __launch_bounds__(TB_A) k_adj_local(Lat L, const R* __restrict__ P, const R* __restrict__ H,
+__global__ void __launch_bounds__(TB_A, 4) k_adj_local(Lat L, const R* __restrict__ P, const R* __restrict__ H,
                                                      const R* __restrict__ geo, const Mom4<R>* __restrict__ jf,
                                                      const R* __restrict__ lPo, const R* __restrict__ lHo,
                                                      Bufs<R> B, R* __restrict__ lHi)
@@ -155,11 +156,11 @@ __global__ void __launch_bounds__(TB_A) k_adj_local(Lat L, const R* __restrict__
     if (face) {
         R ld[9][3];
         gradient_reverse(lD, ld);
+#pragma unroll
         for (int k = 0; k < 9; k++) {
             const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-            const R lp[3] = {ld[k][0], ld[k][1], ld[k][2]}, lm[3] = {-ld[k][0], -ld[k][1], -ld[k][2]};
-            site_reverse(L, x + cx, y + cy, z + cz, lp, B.lJF);
-            site_reverse(L, x - cx, y - cy, z - cz, lm, B.lJF);
+            site_reverse(L, x + cx, y + cy, z + cz, ld[k][0], ld[k][1], ld[k][2], B.lJF);
+            site_reverse(L, x - cx, y - cy, z - cz, -ld[k][0], -ld[k][1], -ld[k][2], B.lJF);
         }
 #pragma unroll
         for (int q = 0; q < 9; q++) B.lD[q * N + v] = R(0);
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(256) k_adj_gather(Lat L, const R* __restrict__
     node_xyz(L, v, x, y, z);
     R lj[3] = {B.lJF[v], B.lJF[N + v], B.lJF[2 * N + v]};
     // interior nodes x' = y - c whose stencil site x' + c is this node
+#pragma unroll
     for (int l = 1; l < Q; l++) {
         const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
         int r[3] = {x - cx, y - cy, z - cz};

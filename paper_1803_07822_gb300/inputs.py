@@ -263,6 +263,27 @@ def periodic_channel(n, tau, umax, n_modes, amp, seed, modes=None, coeffs=None, 
                 chart=channel_chart(n, dfm, layout), faces={}, layout=layout, wall_axis=w)
 
 
+def fourier_modes(kmax, lmax, kmin=1):
+    """The (k, l) pairs k in kmin..kmax along the flow, l in 0..lmax across,
+    phase 0: one deformation coefficient per pair."""
+    k, l = np.meshgrid(np.arange(kmin, kmax + 1), np.arange(0, lmax + 1), indexing="ij")
+    return k.ravel().astype(float), l.ravel().astype(float), np.zeros(k.size)
+
+
+def adjoint_channel(n=(64, 128, 64), kmax=8, lmax=3, seed=5000, tau=0.8, shrink=4.0, umax=0.05, layout=LAYOUT):
+    """Periodic channel whose top-wall displacement is
+    d = H / (shrink sqrt(M)) sum_m c_m cos(2 pi k_m s / L_s + 2 pi l_m p / L_p),
+    M = (kmax) (lmax + 1) coefficients c_m ~ N(0, 0.02) from `seed`; body-force
+    drive for centre-line speed umax.  The defaults (64 x 128 x 64, 32
+    coefficients, shrink 4) keep the largest wall slope at 0.25."""
+    modes = fourier_modes(kmax, lmax)
+    M = len(modes[0])
+    c = np.random.default_rng(seed).normal(0.0, 0.02, M)
+    base = periodic_channel(n, tau, umax, 1, 0.0, 0, layout=layout)  # faces and drive
+    return dict(n=tuple(n), modes=modes, c=c, scale=1.0 / (shrink * np.sqrt(M)), tau=tau, bc_lo=base["bc_lo"],
+                bc_hi=base["bc_hi"], fext=base["fext"], layout=layout)
+
+
 def plain_fp64_channel(n=(16, 32, 16), layout=LAYOUT):
     """Static one-mode channel (16 x 16 x 32 nodes, 32 along the flow):
     d = 0.05 H sin(2 pi s / n_flow), tau = 0.8, body force for umax = 0.05."""

@@ -17,13 +17,7 @@ STEPS, EVERY, H_FD = 200, 20, 1e-4
 
 def case(n, kmax, lmax, seed, tau=0.8, shrink=1.0):
     """d = H / (shrink sqrt(M)) sum_m c_m cos(2 pi k_m s / L_s + 2 pi l_m p / L_p), c_m ~ N(0, 0.02)."""
-    from paper_1803_07822_gb300.adjoint import fourier_modes
-    modes = fourier_modes(kmax, lmax)
-    M = len(modes[0])
-    c = np.random.default_rng(seed).normal(0.0, 0.02, M)
-    base = I.periodic_channel(n, tau, 0.05, 1, 0.0, 0)  # faces, drive; deformation from the coefficients
-    return dict(n=n, modes=modes, c=c, scale=1.0 / (shrink * np.sqrt(M)), tau=tau, bc_lo=base["bc_lo"],
-                bc_hi=base["bc_hi"], fext=base["fext"], layout=I.LAYOUT)
+    return I.adjoint_channel(n, kmax, lmax, seed, tau, shrink)
 
 
 def e_flow(w):
