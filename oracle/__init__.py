@@ -48,7 +48,7 @@ def _load():
             for name in ("orc_geometry", "orc_init", "orc_step", "orc_fill_boundary",
                          "orc_moments", "orc_mass", "orc_wall_force", "orc_transform",
                          "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
-                         "orc_lattice"):
+                         "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian"):
                 getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -77,6 +77,38 @@ def lattice():
     w = np.zeros(19)
     lib.orc_lattice(_p(c), _p(w))
     return c.reshape(19, 3), w
+
+
+def _field_params(n, bc_lo, bc_hi):
+    p = _Params()
+    p.n[:] = list(n)
+    p.bc_lo[:] = list(bc_lo)
+    p.bc_hi[:] = list(bc_lo if bc_hi is None else bc_hi)
+    p.tau, p.theta = 1.0, 1.0 / 3.0
+    return p
+
+
+def lattice_gradient(n, f, order=2, bc_lo=(0, 0, 0), bc_hi=None):
+    """d_k f_c of ncomp fields f [ncomp, N] -> [3, ncomp, N] by the isotropic
+    D3Q19 stencils of App. D, order 2 or 4; non-periodic faces continue the
+    field polynomially (degree = order)."""
+    f = _f64(f)
+    f2 = f.reshape(-1, int(np.prod(n)))
+    out = np.zeros((3, f2.shape[0], f2.shape[1]))
+    p = _field_params(n, bc_lo, bc_hi)
+    if _load().orc_lattice_gradient(ctypes.byref(p), _p(f2), f2.shape[0], int(order), _p(out)):
+        raise ValueError("orc_lattice_gradient: bad order or too few nodes on a non-periodic axis")
+    return out
+
+
+def lattice_laplacian(n, f, order=2, bc_lo=(0, 0, 0), bc_hi=None):
+    """L f_c = (2/c_s^2) sum_l w_l (f(x + c_l) - f(x)) of f [ncomp, N] (App. D)."""
+    f2 = _f64(f).reshape(-1, int(np.prod(n)))
+    out = np.zeros_like(f2)
+    p = _field_params(n, bc_lo, bc_hi)
+    if _load().orc_lattice_laplacian(ctypes.byref(p), _p(f2), f2.shape[0], int(order), _p(out)):
+        raise ValueError("orc_lattice_laplacian: bad order")
+    return out
 
 
 def geometry(n, g6, dg18):

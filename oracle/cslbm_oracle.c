@@ -696,3 +696,108 @@ int orc_transform(const orc_params *p, const double *sqrtg_old, const double *gi
     free(fb);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Isotropic lattice derivatives of a field (App. D) on the D3Q19 set: */
+/*   G_i f(x) = (1/c_s^2) sum_l w_l c_l^i f(x + c_l)             O(dx^2) */
+/*   L f(x)   = (2/c_s^2) sum_l w_l (f(x + c_l) - f(x))           O(dx^2) */
+/*   d_i f(x) = G_i [f - (c_s^2/2) L f](x)                        O(dx^4) */
+/* (the O(dx^4) form: the third-order term of G_i is (c_s^2/2) d_i Lap f */
+/* because the fourth moment of the D3Q19 weights is isotropic).        */
+/* Beyond a non-periodic face the field is continued by the polynomial  */
+/* of degree `order` through the order+1 nodes nearest that face, along */
+/* each out-of-range axis in turn (tensor product at edges, corners).   */
+/* ------------------------------------------------------------------ */
+
+/* Lagrange weights of the polynomial through the nodes 0..d, at point t */
+static void lagrange_at(int d, double t, double *w)
+{
+    for (int i = 0; i <= d; i++) {
+        double num = 1.0, den = 1.0;
+        for (int j = 0; j <= d; j++) {
+            if (j == i) continue;
+            num *= t - j;
+            den *= i - j;
+        }
+        w[i] = num / den;
+    }
+}
+
+/* the continued field at site r (at most two sites outside the domain) */
+static double ext_value(const orc_params *p, const double *f, int order, const int r[3])
+{
+    for (int a = 0; a < 3; a++) {
+        int n = p->n[a];
+        if (r[a] >= 0 && r[a] < n) continue;
+        int bc = r[a] < 0 ? p->bc_lo[a] : p->bc_hi[a];
+        int s[3] = {r[0], r[1], r[2]};
+        if (bc == BC_PERIODIC) {
+            s[a] = ((r[a] % n) + n) % n;
+            return ext_value(p, f, order, s);
+        }
+        /* distance outside the face, counted from the face node inward */
+        double t = r[a] < 0 ? (double)r[a] : (double)(n - 1 - r[a]);
+        double w[5];
+        lagrange_at(order, t, w);
+        double v = 0.0;
+        for (int k = 0; k <= order; k++) {
+            s[a] = r[a] < 0 ? k : n - 1 - k;
+            v += w[k] * ext_value(p, f, order, s);
+        }
+        return v;
+    }
+    return f[idx(p, r[0], r[1], r[2])];
+}
+
+static double lap_value(const orc_params *p, const double *f, int order, const int r[3])
+{
+    double f0 = ext_value(p, f, order, r), s = 0.0;
+    for (int l = 1; l < Q; l++) {
+        int q[3] = {r[0] + CV[l][0], r[1] + CV[l][1], r[2] + CV[l][2]};
+        s += wgt(l) * (ext_value(p, f, order, q) - f0);
+    }
+    return 2.0 / CS2 * s;
+}
+
+/* out[(k*ncomp + c)*N + v] = d_k f_c at node v, order 2 or 4; f is [ncomp][N].
+ * A non-periodic axis needs at least order+1 nodes.                          */
+int orc_lattice_gradient(const orc_params *p, const double *f, int ncomp, int order, double *out)
+{
+    if (order != 2 && order != 4) return -1;
+    for (int a = 0; a < 3; a++)
+        if ((p->bc_lo[a] != BC_PERIODIC || p->bc_hi[a] != BC_PERIODIC) && p->n[a] < order + 1) return -1;
+    long N = nodes(p);
+    for (int c = 0; c < ncomp; c++) {
+        const double *fc = f + (long)c * N;
+#pragma omp parallel for
+        for (long v = 0; v < N; v++) {
+            int r[3];
+            coords(p, v, r);
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int l = 1; l < Q; l++) {
+                int q[3] = {r[0] + CV[l][0], r[1] + CV[l][1], r[2] + CV[l][2]};
+                double val = ext_value(p, fc, order, q);
+                if (order == 4) val -= 0.5 * CS2 * lap_value(p, fc, order, q);
+                for (int k = 0; k < 3; k++) g[k] += wgt(l) * CV[l][k] * val;
+            }
+            for (int k = 0; k < 3; k++) out[((long)k * ncomp + c) * N + v] = g[k] / CS2;
+        }
+    }
+    return 0;
+}
+
+/* L f at node v (the O(dx^2) Laplacian above), f is [ncomp][N]. */
+int orc_lattice_laplacian(const orc_params *p, const double *f, int ncomp, int order, double *out)
+{
+    if (order != 2 && order != 4) return -1;
+    long N = nodes(p);
+    for (int c = 0; c < ncomp; c++) {
+#pragma omp parallel for
+        for (long v = 0; v < N; v++) {
+            int r[3];
+            coords(p, v, r);
+            out[(long)c * N + v] = lap_value(p, f + (long)c * N, order, r);
+        }
+    }
+    return 0;
+}
