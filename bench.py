@@ -401,6 +401,40 @@ def adjoint_report(step_kernel):
             "grad_rel_err_vs_fp64_fd": err, "fd": "central, h = 1e-4, coefficients 0, 9, 27, FP64 GPU forward"}
 
 
+# FP64 operations (an FMA counts 2) per lattice site and field of the
+# lattice-derivative kernels as written: k_lap 18 (subtract + FMA) + 1,
+# k_grad 18 (correction FMA + weight multiply) + 30 accumulations
+LAP_FLOP, GRAD_FLOP = {2: 0, 4: 55}, {2: 48, 4: 84}
+# FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA per clock x 2 x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def lattice_gradient_report(lat, g6, order=4, reps=5):
+    """Device time of the library's lattice gradient (App. D) of the six
+    metric components on the bench lattice, against the FP64 peak."""
+    import torch
+    for _ in range(2):
+        lat.lattice_gradient(g6, order)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        lat.lattice_gradient(g6, order)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    N = lat.N
+    pad = [(1 if order == 4 and not (lo == 0 and hi == 0) else 0) for lo, hi in zip(list(lat.params.bc_lo), list(lat.params.bc_hi))]
+    Ne = int(np.prod([k + 2 * p for k, p in zip(lat.n, pad)]))
+    flop = 6 * (LAP_FLOP[order] * Ne + GRAD_FLOP[order] * N)
+    nbytes = 6 * 8 * (N + (2 * Ne if order == 4 else 0)) + 18 * 8 * N
+    gf = flop / (ms * 1e-3) / 1e9
+    return {"order": order, "fields": 6, "nodes": N, "ms": ms, "flop_per_node": flop / N,
+            "bytes_per_node": nbytes / N, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "alu", "achieved": gf, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                         "frac": gf / FP64_PEAK_GFLOPS, "peak_kind": "derived from unit counts and clock"}}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -530,6 +564,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1:
+        line["lattice_gradient"] = lattice_gradient_report(lat, dev[0]["g6"])
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -234,6 +234,43 @@ cslbm_status cslbm_adjoint_metric_grad(cslbm_ctx* ctx, const double* g6, const d
                                        double* grad_dg18, double* grad_J9);
 
 /* ---------------------------------------------------------------------------
+ * Isotropic lattice derivatives (App. D, improved lattice derivatives): with
+ * the D3Q19 weights w and velocities c,
+ *   G_i f = (1/c_s^2) sum_l w_l c_l^i f(x + c_l)          (order 2)
+ *   L f   = (2/c_s^2) sum_l w_l (f(x + c_l) - f(x))       (the Laplacian)
+ *   d_i f = G_i[f - (c_s^2/2) L f]                       (order 4)
+ * Beyond a non-periodic face a field is continued by the polynomial of degree
+ * `order` through the order + 1 nodes nearest the face, axis by axis.  FP64,
+ * on the context's stream.  Every pointer is device memory (EINVAL
+ * otherwise); an axis with a non-periodic face needs order + 1 nodes and
+ * every axis 2 (EINVAL).
+ * ------------------------------------------------------------------------- */
+
+/* Scratch bytes of cslbm_lattice_gradient for ncomp fields (0 for order 2;
+ * order 4 keeps L f on the lattice padded by one site at non-periodic faces). */
+cslbm_status cslbm_lattice_gradient_scratch_bytes(const cslbm_ctx* ctx, int ncomp, int order, size_t* bytes);
+
+/* grad[(k ncomp + c) N + v] = d_k f_c at node v for the fields f [ncomp][N]
+ * (layout of the context's lattice), order 2 or 4.  For ncomp = 6 and f = g6
+ * the output is dg18 in the layout cslbm_set_metric takes.  Asynchronous;
+ * ENOMEM for a short scratch (caller-owned, device memory). */
+cslbm_status cslbm_lattice_gradient(cslbm_ctx* ctx, const double* f, int ncomp, int order, double* grad,
+                                    void* scratch, size_t scratch_bytes);
+
+/* Scratch bytes of cslbm_set_metric_lattice / cslbm_update_metric_lattice:
+ * 18 N doubles of dg plus the gradient's own scratch for 6 fields. */
+cslbm_status cslbm_metric_lattice_scratch_bytes(const cslbm_ctx* ctx, int order, size_t* bytes);
+
+/* cslbm_set_metric / cslbm_update_metric with dg computed from g6 on the
+ * lattice (order 2 or 4) instead of supplied: the geometry from the metric
+ * alone (App. D: metric, Christoffel symbols precomputed at fourth order).
+ * g6 (and Jnew9) are device memory. */
+cslbm_status cslbm_set_metric_lattice(cslbm_ctx* ctx, const double* g6, int order, void* scratch,
+                                      size_t scratch_bytes);
+cslbm_status cslbm_update_metric_lattice(cslbm_ctx* ctx, const double* g6, const double* Jnew9, int order,
+                                         void* scratch, size_t scratch_bytes);
+
+/* ---------------------------------------------------------------------------
  * Batched form: nb independent channels (each its own cslbm_params, FP32
  * storage, any sizes) advanced together.  Each channel is an ordinary
  * context, reachable with cslbm_batch_context, on which every call above

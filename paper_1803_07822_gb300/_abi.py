@@ -64,6 +64,11 @@ SIGNATURES = {
     "cslbm_step_backward": [_P],
     "cslbm_adjoint_init_backward": [_P],
     "cslbm_adjoint_metric_grad": [_P, _P, _P, _P, _P, _P],
+    "cslbm_lattice_gradient_scratch_bytes": [_P, _I, _I, ctypes.POINTER(_SZ)],
+    "cslbm_lattice_gradient": [_P, _P, _I, _I, _P, _P, _SZ],
+    "cslbm_metric_lattice_scratch_bytes": [_P, _I, ctypes.POINTER(_SZ)],
+    "cslbm_set_metric_lattice": [_P, _P, _I, _P, _SZ],
+    "cslbm_update_metric_lattice": [_P, _P, _P, _I, _P, _SZ],
     "cslbm_batch_workspace_bytes": [_I, ctypes.POINTER(Params), ctypes.POINTER(_SZ)],
     "cslbm_batch_create": [_I, ctypes.POINTER(Params), _P, _SZ, _P, ctypes.POINTER(_P)],
     "cslbm_batch_context": [_P, _I, ctypes.POINTER(_P)],

@@ -1,0 +1,295 @@
+// Isotropic lattice derivatives of FP64 fields (App. D) on the device, and
+// the geometry of a context from its metric alone.
+//
+// With the D3Q19 weights w_l and velocities c_l (lattice units):
+//   G_i f(x) = (1/c_s^2) sum_l w_l c_l^i f(x + c_l)            second order
+//   L f(x)   = (2/c_s^2) sum_l w_l (f(x + c_l) - f(x))         second order
+//   d_i f(x) = G_i[f - (c_s^2/2) L f](x)                        fourth order
+// (the third-order term of G_i is (c_s^2/2) d_i Lap f: the fourth moment of
+// the D3Q19 weights is isotropic).  Beyond a non-periodic face the field is
+// continued by the polynomial of degree `order` through the order + 1 nodes
+// nearest the face, axis by axis (tensor product at edges and corners).
+//
+// Two kernels: k_lap writes L f on the lattice padded by one site along every
+// axis with a non-periodic face (order 4 only), k_grad forms the gradient at
+// every node.  One thread per (node or padded site, component); FP64
+// throughout, so both are bound by the FP64 rate, not by HBM.
+#include <cstdint>
+#include <string>
+
+#include "ctx.h"
+#include "lbm_device.cuh"
+
+cslbm_status cslbm_record_error(cslbm_status s, const char* msg);
+
+namespace cslbm {
+namespace lder {
+
+constexpr int TBL = 256;
+constexpr double kCs2 = 1.0 / 3.0;
+
+struct Box {
+    int n[3];
+    int plo[3], phi[3];  // low / high face periodic
+    int pad[3];          // 1 on an axis with a non-periodic face
+    int ne[3];           // padded extents n + 2 pad
+    long long N, Ne;
+};
+
+// Weight of node k (k = 0 the face node, counting inward) in the value t = 1
+// or 2 sites beyond the face: the polynomial of degree `order` through the
+// nodes 0..order, evaluated at -t (Lagrange form, worked out).
+__device__ __forceinline__ double cont_weight(int order, int t, int k)
+{
+    if (order == 2) {
+        const double a[3] = {3.0, -3.0, 1.0}, b[3] = {6.0, -8.0, 3.0};
+        return t == 1 ? a[k] : b[k];
+    }
+    const double a[5] = {5.0, -10.0, 10.0, -5.0, 1.0}, b[5] = {15.0, -40.0, 45.0, -24.0, 5.0};
+    return t == 1 ? a[k] : b[k];
+}
+
+__device__ __forceinline__ bool wrap(const Box& B, int a, int& r)
+{
+    if (r < 0 && B.plo[a]) r += B.n[a];
+    else if (r >= B.n[a] && B.phi[a]) r -= B.n[a];
+    return r >= 0 && r < B.n[a];
+}
+
+// the continued field at a site up to two steps beyond a face: the terms of
+// every out-of-range axis multiplied out
+__device__ __noinline__ double site_far(const Box& B, const double* __restrict__ f, int order, int x, int y, int z)
+{
+    int c[3][5], m[3];
+    double w[3][5];
+    const int r[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int ra = r[a];
+        if (wrap(B, a, ra)) {
+            m[a] = 1;
+            c[a][0] = ra;
+            w[a][0] = 1.0;
+            continue;
+        }
+        const bool lo = ra < 0;
+        const int t = lo ? -ra : ra - (B.n[a] - 1);
+        m[a] = order + 1;
+        for (int k = 0; k <= order; k++) {
+            c[a][k] = lo ? k : B.n[a] - 1 - k;
+            w[a][k] = cont_weight(order, t, k);
+        }
+    }
+    double v = 0.0;
+    for (int k = 0; k < m[2]; k++)
+        for (int j = 0; j < m[1]; j++) {
+            double row = 0.0;
+            const long long base = ((long long)c[2][k] * B.n[1] + c[1][j]) * B.n[0];
+            for (int i = 0; i < m[0]; i++) row += w[0][i] * f[base + c[0][i]];
+            v += w[2][k] * w[1][j] * row;
+        }
+    return v;
+}
+
+__device__ __forceinline__ double site(const Box& B, const double* __restrict__ f, int order, int x, int y, int z)
+{
+    int xs = x, ys = y, zs = z;
+    if (wrap(B, 0, xs) && wrap(B, 1, ys) && wrap(B, 2, zs))
+        return __ldg(f + ((long long)zs * B.n[1] + ys) * B.n[0] + xs);
+    return site_far(B, f, order, x, y, z);
+}
+
+// a site whose whole stencil resolves without continuation (periodic wrap only)
+__device__ __forceinline__ bool inner(const Box& B, int a, int r)
+{
+    return r >= 0 && r < B.n[a] && (r >= 1 || B.plo[a]) && (r <= B.n[a] - 2 || B.phi[a]);
+}
+__device__ __forceinline__ long long nb_index(const Box& B, int x, int y, int z)
+{
+    wrap(B, 0, x);
+    wrap(B, 1, y);
+    wrap(B, 2, z);
+    return ((long long)z * B.n[1] + y) * B.n[0] + x;
+}
+
+// L f at every site of the padded lattice, component blockIdx.y
+__global__ void __launch_bounds__(TBL) k_lap(const __grid_constant__ Box B, const double* __restrict__ f, int order,
+                                             double* __restrict__ lap)
+{
+    const long long s = blockIdx.x * (long long)TBL + threadIdx.x;
+    if (s >= B.Ne) return;
+    const double* fc = f + (long long)blockIdx.y * B.N;
+    const long long row = s / B.ne[0];
+    const int x = (int)(s - row * B.ne[0]) - B.pad[0];
+    const int y = (int)(row % B.ne[1]) - B.pad[1];
+    const int z = (int)(row / B.ne[1]) - B.pad[2];
+    double acc = 0.0;
+    if (inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z)) {
+        const double f0 = __ldg(fc + ((long long)z * B.n[1] + y) * B.n[0] + x);
+#pragma unroll
+        for (int l = 1; l < Q; l++)
+            acc += wq(l) * (__ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2))) - f0);
+    } else {
+        const double f0 = site(B, fc, order, x, y, z);
+#pragma unroll
+        for (int l = 1; l < Q; l++)
+            acc += wq(l) * (site(B, fc, order, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)) - f0);
+    }
+    lap[(long long)blockIdx.y * B.Ne + s] = (2.0 / kCs2) * acc;
+}
+
+// L f at a site at most one step beyond a face, from the padded field
+__device__ __forceinline__ double lap_at(const Box& B, const double* __restrict__ lapc, int x, int y, int z)
+{
+    int r[3] = {x, y, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++) wrap(B, a, r[a]);
+    return __ldg(lapc + ((long long)(r[2] + B.pad[2]) * B.ne[1] + (r[1] + B.pad[1])) * B.ne[0] + (r[0] + B.pad[0]));
+}
+
+// d_k f_c at every node: out[(k ncomp + c) N + v]
+__global__ void __launch_bounds__(TBL) k_grad(const __grid_constant__ Box B, const double* __restrict__ f, int ncomp,
+                                              int order, const double* __restrict__ lap, double* __restrict__ out)
+{
+    const long long v = blockIdx.x * (long long)TBL + threadIdx.x;
+    if (v >= B.N) return;
+    const int c = blockIdx.y;
+    const double* fc = f + (long long)c * B.N;
+    const double* lc = lap + (long long)c * B.Ne;
+    const long long row = v / B.n[0];
+    const int x = (int)(v - row * B.n[0]), y = (int)(row % B.n[1]), z = (int)(row / B.n[1]);
+    const bool fast = inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+#pragma unroll
+    for (int l = 1; l < Q; l++) {
+        const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        double val = fast ? __ldg(fc + nb_index(B, x + cx, y + cy, z + cz)) : site_far(B, fc, order, x + cx, y + cy, z + cz);
+        if (order == 4) val -= 0.5 * kCs2 * lap_at(B, lc, x + cx, y + cy, z + cz);
+        const double wv = wq(l) * val;
+        if (cx) g0 += cx * wv;
+        if (cy) g1 += cy * wv;
+        if (cz) g2 += cz * wv;
+    }
+    out[((long long)0 * ncomp + c) * B.N + v] = g0 / kCs2;
+    out[((long long)1 * ncomp + c) * B.N + v] = g1 / kCs2;
+    out[((long long)2 * ncomp + c) * B.N + v] = g2 / kCs2;
+}
+
+Box box_of(const cslbm_ctx* c, int order)
+{
+    Box B;
+    B.N = c->N;
+    B.Ne = 1;
+    for (int a = 0; a < 3; a++) {
+        B.n[a] = c->n[a];
+        B.plo[a] = c->p.bc_lo[a] == CSLBM_PERIODIC;
+        B.phi[a] = c->p.bc_hi[a] == CSLBM_PERIODIC;
+        B.pad[a] = (order == 4 && !(B.plo[a] && B.phi[a])) ? 1 : 0;
+        B.ne[a] = B.n[a] + 2 * B.pad[a];
+        B.Ne *= B.ne[a];
+    }
+    return B;
+}
+
+cslbm_status lfail(cslbm_status s, const std::string& m) { return cslbm_record_error(s, m.c_str()); }
+
+cslbm_status check_order(const cslbm_ctx* c, int order)
+{
+    if (order != 2 && order != 4) return lfail(CSLBM_EINVAL, "order must be 2 or 4");
+    for (int a = 0; a < 3; a++)
+        if (c->n[a] < 2) return lfail(CSLBM_EINVAL, "every axis needs at least 2 nodes");
+    for (int a = 0; a < 3; a++)
+        if ((c->p.bc_lo[a] != CSLBM_PERIODIC || c->p.bc_hi[a] != CSLBM_PERIODIC) && c->n[a] < order + 1)
+            return lfail(CSLBM_EINVAL, "an axis with a non-periodic face needs at least order + 1 nodes");
+    return CSLBM_OK;
+}
+
+bool device_memory(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t lap_bytes(const cslbm_ctx* c, int ncomp, int order)
+{
+    return order == 4 ? (size_t)ncomp * (size_t)box_of(c, order).Ne * sizeof(double) : 0;
+}
+
+cslbm_status gradient(cslbm_ctx* c, const double* f, int ncomp, int order, double* out, void* scratch, size_t bytes)
+{
+    if (!c || !f || !out || ncomp < 1 || ncomp > 65535) return lfail(CSLBM_EINVAL, "bad argument");
+    if (cslbm_status s = check_order(c, order)) return s;
+    const size_t need = lap_bytes(c, ncomp, order);
+    if (need && (!scratch || bytes < need)) return lfail(CSLBM_ENOMEM, "scratch smaller than required");
+    if (!device_memory(f) || !device_memory(out) || (need && !device_memory(scratch)))
+        return lfail(CSLBM_EINVAL, "fields, output and scratch must be device memory");
+    const Box B = box_of(c, order);
+    double* lap = (double*)scratch;
+    if (order == 4)
+        k_lap<<<dim3((unsigned)((B.Ne + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, f, order, lap);
+    k_grad<<<dim3((unsigned)((B.N + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, f, ncomp, order, lap,
+                                                                                          out);
+    c->launches += order == 4 ? 2 : 1;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lfail(CSLBM_ECUDA, std::string("lattice gradient: ") + cudaGetErrorString(e));
+    return CSLBM_OK;
+}
+
+}  // namespace lder
+}  // namespace cslbm
+
+using namespace cslbm::lder;
+
+extern "C" {
+
+cslbm_status cslbm_lattice_gradient_scratch_bytes(const cslbm_ctx* c, int ncomp, int order, size_t* bytes)
+{
+    if (!c || !bytes || ncomp < 1) return lfail(CSLBM_EINVAL, "bad argument");
+    if (cslbm_status s = check_order(c, order)) return s;
+    *bytes = lap_bytes(c, ncomp, order);
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_lattice_gradient(cslbm_ctx* c, const double* f, int ncomp, int order, double* grad, void* scratch,
+                                    size_t scratch_bytes)
+{
+    return gradient(c, f, ncomp, order, grad, scratch, scratch_bytes);
+}
+
+cslbm_status cslbm_metric_lattice_scratch_bytes(const cslbm_ctx* c, int order, size_t* bytes)
+{
+    if (!c || !bytes) return lfail(CSLBM_EINVAL, "bad argument");
+    if (cslbm_status s = check_order(c, order)) return s;
+    *bytes = 18 * (size_t)c->N * sizeof(double) + lap_bytes(c, 6, order);
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_set_metric_lattice(cslbm_ctx* c, const double* g6, int order, void* scratch, size_t scratch_bytes)
+{
+    size_t need = 0;
+    if (cslbm_status s = cslbm_metric_lattice_scratch_bytes(c, order, &need)) return s;
+    if (!g6 || !scratch || scratch_bytes < need) return lfail(CSLBM_ENOMEM, "scratch smaller than required");
+    double* dg = (double*)scratch;
+    const size_t dg_bytes = 18 * (size_t)c->N * sizeof(double);
+    if (cslbm_status s = gradient(c, g6, 6, order, dg, (char*)scratch + dg_bytes, scratch_bytes - dg_bytes)) return s;
+    return cslbm_set_metric(c, g6, dg, 1);
+}
+
+cslbm_status cslbm_update_metric_lattice(cslbm_ctx* c, const double* g6, const double* Jnew9, int order, void* scratch,
+                                         size_t scratch_bytes)
+{
+    size_t need = 0;
+    if (cslbm_status s = cslbm_metric_lattice_scratch_bytes(c, order, &need)) return s;
+    if (!g6 || !Jnew9 || !scratch || scratch_bytes < need) return lfail(CSLBM_ENOMEM, "scratch smaller than required");
+    if (!device_memory(Jnew9)) return lfail(CSLBM_EINVAL, "Jnew9 must be device memory");
+    double* dg = (double*)scratch;
+    const size_t dg_bytes = 18 * (size_t)c->N * sizeof(double);
+    if (cslbm_status s = gradient(c, g6, 6, order, dg, (char*)scratch + dg_bytes, scratch_bytes - dg_bytes)) return s;
+    return cslbm_update_metric(c, g6, dg, Jnew9, 1);
+}
+
+}  // extern "C"

@@ -99,6 +99,46 @@ class CurvedLattice:
             raise ValueError("metric inputs must all be host or all device arrays")
         call("cslbm_update_metric", self.ctx, p1, p2, p3, d1)
 
+    # -- lattice derivatives (App. D) ----------------------------------------
+    def _dev64(self, a, rows):
+        torch = _torch()
+        t = torch.as_tensor(a, dtype=torch.float64, device=self.device).reshape(rows, self.N).contiguous()
+        return t
+
+    def lattice_gradient(self, f, order=4):
+        """d_k f_c of fields f [ncomp, N] (FP64; host or device) on this
+        lattice -> CUDA tensor [3, ncomp, N], by the library's stencils."""
+        torch = _torch()
+        f = self._dev64(f, -1 if getattr(f, "ndim", 1) > 1 else 1)
+        ncomp = f.shape[0]
+        nb = ctypes.c_size_t(0)
+        call("cslbm_lattice_gradient_scratch_bytes", self.ctx, ncomp, int(order), ctypes.byref(nb))
+        scratch = torch.empty(max(nb.value, 8), dtype=torch.uint8, device=self.device)
+        out = torch.empty((3, ncomp, self.N), dtype=torch.float64, device=self.device)
+        call("cslbm_lattice_gradient", self.ctx, f.data_ptr(), ncomp, int(order), out.data_ptr(), scratch.data_ptr(),
+             scratch.numel())
+        return out
+
+    def _metric_scratch(self, order):
+        torch = _torch()
+        nb = ctypes.c_size_t(0)
+        call("cslbm_metric_lattice_scratch_bytes", self.ctx, int(order), ctypes.byref(nb))
+        return torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+
+    def set_metric_lattice(self, g6, order=4):
+        """set_metric with dg computed from g6 on the lattice."""
+        g = self._dev64(g6, 6)
+        scratch = self._metric_scratch(order)
+        call("cslbm_set_metric_lattice", self.ctx, g.data_ptr(), int(order), scratch.data_ptr(), scratch.numel())
+
+    def update_metric_lattice(self, g6, J9, order=4):
+        """update_metric (metric change + transformation) with dg from g6 on the lattice."""
+        g = self._dev64(g6, 6)
+        J = self._dev64(J9, 9)
+        scratch = self._metric_scratch(order)
+        call("cslbm_update_metric_lattice", self.ctx, g.data_ptr(), J.data_ptr(), int(order), scratch.data_ptr(),
+             scratch.numel())
+
     def set_chart(self, chart):
         """Metric and Jacobian of an inputs.Chart (no transformation)."""
         self.set_metric(chart.g6, chart.dg18)
