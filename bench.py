@@ -402,9 +402,9 @@ def adjoint_report(step_kernel):
 
 
 # FP64 operations (an FMA counts 2) per lattice site and field of the
-# lattice-derivative kernels as written: k_lap 18 (subtract + FMA) + 1,
-# k_grad 18 (correction FMA + weight multiply) + 30 accumulations
-LAP_FLOP, GRAD_FLOP = {2: 0, 4: 55}, {2: 48, 4: 84}
+# lattice-derivative kernels as written: k_pad 18 (subtract + FMA) + 1 per
+# padded site (order 4), k_grad 9 pair differences + 15 FMAs per node
+LAP_FLOP, GRAD_FLOP = {2: 0, 4: 55}, {2: 39, 4: 39}
 # FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA per clock x 2 x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
@@ -424,10 +424,10 @@ def lattice_gradient_report(lat, g6, order=4, reps=5):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     N = lat.N
-    pad = [(1 if order == 4 and not (lo == 0 and hi == 0) else 0) for lo, hi in zip(list(lat.params.bc_lo), list(lat.params.bc_hi))]
+    pad = [(0 if (lo == 0 and hi == 0) else 1) for lo, hi in zip(list(lat.params.bc_lo), list(lat.params.bc_hi))]
     Ne = int(np.prod([k + 2 * p for k, p in zip(lat.n, pad)]))
     flop = 6 * (LAP_FLOP[order] * Ne + GRAD_FLOP[order] * N)
-    nbytes = 6 * 8 * (N + (2 * Ne if order == 4 else 0)) + 18 * 8 * N
+    nbytes = 6 * 8 * (N + 2 * Ne) + 18 * 8 * N
     gf = flop / (ms * 1e-3) / 1e9
     return {"order": order, "fields": 6, "nodes": N, "ms": ms, "flop_per_node": flop / N,
             "bytes_per_node": nbytes / N, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,

@@ -246,8 +246,9 @@ cslbm_status cslbm_adjoint_metric_grad(cslbm_ctx* ctx, const double* g6, const d
  * every axis 2 (EINVAL).
  * ------------------------------------------------------------------------- */
 
-/* Scratch bytes of cslbm_lattice_gradient for ncomp fields (0 for order 2;
- * order 4 keeps L f on the lattice padded by one site at non-periodic faces). */
+/* Scratch bytes of cslbm_lattice_gradient for ncomp fields: F = f - (c_s^2/2)
+ * L f (order 4) or the continued f (order 2) on the lattice padded by one
+ * site at non-periodic faces, ncomp x padded nodes doubles. */
 cslbm_status cslbm_lattice_gradient_scratch_bytes(const cslbm_ctx* ctx, int ncomp, int order, size_t* bytes);
 
 /* grad[(k ncomp + c) N + v] = d_k f_c at node v for the fields f [ncomp][N]

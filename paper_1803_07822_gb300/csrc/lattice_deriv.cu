@@ -10,10 +10,10 @@
 // continued by the polynomial of degree `order` through the order + 1 nodes
 // nearest the face, axis by axis (tensor product at edges and corners).
 //
-// Two kernels: k_lap writes L f on the lattice padded by one site along every
-// axis with a non-periodic face (order 4 only), k_grad forms the gradient at
-// every node.  One thread per (node or padded site, component); FP64
-// throughout, so both are bound by the FP64 rate, not by HBM.
+// Two kernels: k_pad writes F = f - (c_s^2/2) L f (order 4) or the continued f
+// (order 2) on the lattice padded by one site along every axis with a
+// non-periodic face, k_grad forms G_i F at every node from the nine opposite
+// pairs.  One thread per (padded site or node, component); FP64 throughout.
 #include <cstdint>
 #include <string>
 
@@ -112,9 +112,11 @@ __device__ __forceinline__ long long nb_index(const Box& B, int x, int y, int z)
     return ((long long)z * B.n[1] + y) * B.n[0] + x;
 }
 
-// L f at every site of the padded lattice, component blockIdx.y
-__global__ void __launch_bounds__(TBL) k_lap(const __grid_constant__ Box B, const double* __restrict__ f, int order,
-                                             double* __restrict__ lap)
+// F = f - (c_s^2/2) L f = f0 - sum_l w_l (f_l - f0) (order 4), or the
+// continued f (order 2), at every site of the padded lattice; component
+// blockIdx.y
+__global__ void __launch_bounds__(TBL) k_pad(const __grid_constant__ Box B, const double* __restrict__ f, int order,
+                                             double* __restrict__ F)
 {
     const long long s = blockIdx.x * (long long)TBL + threadIdx.x;
     if (s >= B.Ne) return;
@@ -123,56 +125,62 @@ __global__ void __launch_bounds__(TBL) k_lap(const __grid_constant__ Box B, cons
     const int x = (int)(s - row * B.ne[0]) - B.pad[0];
     const int y = (int)(row % B.ne[1]) - B.pad[1];
     const int z = (int)(row / B.ne[1]) - B.pad[2];
-    double acc = 0.0;
+    double out;
     if (inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z)) {
         const double f0 = __ldg(fc + ((long long)z * B.n[1] + y) * B.n[0] + x);
+        double acc = 0.0;
+        if (order == 4) {
 #pragma unroll
-        for (int l = 1; l < Q; l++)
-            acc += wq(l) * (__ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2))) - f0);
+            for (int l = 1; l < Q; l++)
+                acc += wq(l) * (__ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2))) - f0);
+        }
+        out = f0 - acc;
     } else {
         const double f0 = site(B, fc, order, x, y, z);
+        double acc = 0.0;
+        if (order == 4) {
 #pragma unroll
-        for (int l = 1; l < Q; l++)
-            acc += wq(l) * (site(B, fc, order, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)) - f0);
+            for (int l = 1; l < Q; l++)
+                acc += wq(l) * (site(B, fc, order, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)) - f0);
+        }
+        out = f0 - acc;
     }
-    lap[(long long)blockIdx.y * B.Ne + s] = (2.0 / kCs2) * acc;
+    F[(long long)blockIdx.y * B.Ne + s] = out;
 }
 
-// L f at a site at most one step beyond a face, from the padded field
-__device__ __forceinline__ double lap_at(const Box& B, const double* __restrict__ lapc, int x, int y, int z)
+// a site at most one step beyond a face, in the padded lattice
+__device__ __forceinline__ long long pad_index(const Box& B, int x, int y, int z)
 {
-    int r[3] = {x, y, z};
-#pragma unroll
-    for (int a = 0; a < 3; a++) wrap(B, a, r[a]);
-    return __ldg(lapc + ((long long)(r[2] + B.pad[2]) * B.ne[1] + (r[1] + B.pad[1])) * B.ne[0] + (r[0] + B.pad[0]));
+    wrap(B, 0, x);
+    wrap(B, 1, y);
+    wrap(B, 2, z);
+    return ((long long)(z + B.pad[2]) * B.ne[1] + (y + B.pad[1])) * B.ne[0] + (x + B.pad[0]);
 }
 
-// d_k f_c at every node: out[(k ncomp + c) N + v]
-__global__ void __launch_bounds__(TBL) k_grad(const __grid_constant__ Box B, const double* __restrict__ f, int ncomp,
-                                              int order, const double* __restrict__ lap, double* __restrict__ out)
+// d_k f_c = G_k F at every node, over the nine opposite pairs:
+// out[(k ncomp + c) N + v]
+__global__ void __launch_bounds__(TBL) k_grad(const __grid_constant__ Box B, int ncomp, const double* __restrict__ F,
+                                              double* __restrict__ out)
 {
     const long long v = blockIdx.x * (long long)TBL + threadIdx.x;
     if (v >= B.N) return;
     const int c = blockIdx.y;
-    const double* fc = f + (long long)c * B.N;
-    const double* lc = lap + (long long)c * B.Ne;
+    const double* Fc = F + (long long)c * B.Ne;
     const long long row = v / B.n[0];
     const int x = (int)(v - row * B.n[0]), y = (int)(row % B.n[1]), z = (int)(row / B.n[1]);
-    const bool fast = inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z);
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
 #pragma unroll
-    for (int l = 1; l < Q; l++) {
-        const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-        double val = fast ? __ldg(fc + nb_index(B, x + cx, y + cy, z + cz)) : site_far(B, fc, order, x + cx, y + cy, z + cz);
-        if (order == 4) val -= 0.5 * kCs2 * lap_at(B, lc, x + cx, y + cy, z + cz);
-        const double wv = wq(l) * val;
-        if (cx) g0 += cx * wv;
-        if (cy) g1 += cy * wv;
-        if (cz) g2 += cz * wv;
+    for (int k = 0; k < 9; k++) {
+        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        const double d = __ldg(Fc + pad_index(B, x + cx, y + cy, z + cz)) - __ldg(Fc + pad_index(B, x - cx, y - cy, z - cz));
+        const double wd = wq(l) / kCs2;
+        if (cx) g0 = fma(cx * wd, d, g0);
+        if (cy) g1 = fma(cy * wd, d, g1);
+        if (cz) g2 = fma(cz * wd, d, g2);
     }
-    out[((long long)0 * ncomp + c) * B.N + v] = g0 / kCs2;
-    out[((long long)1 * ncomp + c) * B.N + v] = g1 / kCs2;
-    out[((long long)2 * ncomp + c) * B.N + v] = g2 / kCs2;
+    out[((long long)0 * ncomp + c) * B.N + v] = g0;
+    out[((long long)1 * ncomp + c) * B.N + v] = g1;
+    out[((long long)2 * ncomp + c) * B.N + v] = g2;
 }
 
 Box box_of(const cslbm_ctx* c, int order)
@@ -184,7 +192,7 @@ Box box_of(const cslbm_ctx* c, int order)
         B.n[a] = c->n[a];
         B.plo[a] = c->p.bc_lo[a] == CSLBM_PERIODIC;
         B.phi[a] = c->p.bc_hi[a] == CSLBM_PERIODIC;
-        B.pad[a] = (order == 4 && !(B.plo[a] && B.phi[a])) ? 1 : 0;
+        B.pad[a] = (B.plo[a] && B.phi[a]) ? 0 : 1;
         B.ne[a] = B.n[a] + 2 * B.pad[a];
         B.Ne *= B.ne[a];
     }
@@ -214,26 +222,24 @@ bool device_memory(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-size_t lap_bytes(const cslbm_ctx* c, int ncomp, int order)
+size_t pad_bytes(const cslbm_ctx* c, int ncomp, int order)
 {
-    return order == 4 ? (size_t)ncomp * (size_t)box_of(c, order).Ne * sizeof(double) : 0;
+    return (size_t)ncomp * (size_t)box_of(c, order).Ne * sizeof(double);
 }
 
 cslbm_status gradient(cslbm_ctx* c, const double* f, int ncomp, int order, double* out, void* scratch, size_t bytes)
 {
     if (!c || !f || !out || ncomp < 1 || ncomp > 65535) return lfail(CSLBM_EINVAL, "bad argument");
     if (cslbm_status s = check_order(c, order)) return s;
-    const size_t need = lap_bytes(c, ncomp, order);
-    if (need && (!scratch || bytes < need)) return lfail(CSLBM_ENOMEM, "scratch smaller than required");
-    if (!device_memory(f) || !device_memory(out) || (need && !device_memory(scratch)))
+    const size_t need = pad_bytes(c, ncomp, order);
+    if (!scratch || bytes < need) return lfail(CSLBM_ENOMEM, "scratch smaller than required");
+    if (!device_memory(f) || !device_memory(out) || !device_memory(scratch))
         return lfail(CSLBM_EINVAL, "fields, output and scratch must be device memory");
     const Box B = box_of(c, order);
-    double* lap = (double*)scratch;
-    if (order == 4)
-        k_lap<<<dim3((unsigned)((B.Ne + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, f, order, lap);
-    k_grad<<<dim3((unsigned)((B.N + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, f, ncomp, order, lap,
-                                                                                          out);
-    c->launches += order == 4 ? 2 : 1;
+    double* F = (double*)scratch;
+    k_pad<<<dim3((unsigned)((B.Ne + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, f, order, F);
+    k_grad<<<dim3((unsigned)((B.N + TBL - 1) / TBL), (unsigned)ncomp), TBL, 0, c->stream>>>(B, ncomp, F, out);
+    c->launches += 2;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return lfail(CSLBM_ECUDA, std::string("lattice gradient: ") + cudaGetErrorString(e));
     return CSLBM_OK;
@@ -250,7 +256,7 @@ cslbm_status cslbm_lattice_gradient_scratch_bytes(const cslbm_ctx* c, int ncomp,
 {
     if (!c || !bytes || ncomp < 1) return lfail(CSLBM_EINVAL, "bad argument");
     if (cslbm_status s = check_order(c, order)) return s;
-    *bytes = lap_bytes(c, ncomp, order);
+    *bytes = pad_bytes(c, ncomp, order);
     return CSLBM_OK;
 }
 
@@ -264,7 +270,7 @@ cslbm_status cslbm_metric_lattice_scratch_bytes(const cslbm_ctx* c, int order, s
 {
     if (!c || !bytes) return lfail(CSLBM_EINVAL, "bad argument");
     if (cslbm_status s = check_order(c, order)) return s;
-    *bytes = 18 * (size_t)c->N * sizeof(double) + lap_bytes(c, 6, order);
+    *bytes = 18 * (size_t)c->N * sizeof(double) + pad_bytes(c, 6, order);
     return CSLBM_OK;
 }
 

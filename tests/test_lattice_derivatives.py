@@ -132,6 +132,14 @@ def test_errors():
     from paper_1803_07822_gb300._abi import call
     import torch
     out = torch.empty((3, lat.N), dtype=torch.float64, device="cuda")
+    nb = ctypes.c_size_t(0)
+    call("cslbm_lattice_gradient_scratch_bytes", lat.ctx, 1, 2, ctypes.byref(nb))
+    scratch = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
     with pytest.raises(CslbmError) as ex:
-        call("cslbm_lattice_gradient", lat.ctx, f.ctypes.data_as(ctypes.c_void_p), 1, 2, out.data_ptr(), None, 0)
+        call("cslbm_lattice_gradient", lat.ctx, f.ctypes.data_as(ctypes.c_void_p), 1, 2, out.data_ptr(),
+             scratch.data_ptr(), nb.value)
     assert ex.value.status == EINVAL
+    with pytest.raises(CslbmError) as ex:  # a short scratch
+        call("cslbm_lattice_gradient", lat.ctx, torch.zeros(lat.N, dtype=torch.float64, device="cuda").data_ptr(), 1,
+             2, out.data_ptr(), scratch.data_ptr(), nb.value - 8)
+    assert ex.value.status == 3  # ENOMEM
