@@ -402,9 +402,9 @@ def adjoint_report(step_kernel):
 
 
 # FP64 operations (an FMA counts 2) per lattice site and field of the
-# lattice-derivative kernels as written: k_pad 18 (subtract + FMA) + 1 per
-# padded site (order 4), k_grad 9 pair differences + 15 FMAs per node
-LAP_FLOP, GRAD_FLOP = {2: 0, 4: 55}, {2: 39, 4: 39}
+# lattice-derivative kernels as written: k_pad 16 additions + 2 FMAs + 1
+# multiply per padded site (order 4), k_grad 9 pair differences + 15 FMAs
+LAP_FLOP, GRAD_FLOP = {2: 0, 4: 21}, {2: 39, 4: 39}
 # FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA per clock x 2 x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 

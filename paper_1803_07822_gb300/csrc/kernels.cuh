@@ -275,11 +275,13 @@ __global__ void __launch_bounds__(TPB) k_forcing(Lat L, const S* __restrict__ P,
     for (int k = 0; k < 3; k++)
 #pragma unroll
         for (int i = 0; i < 3; i++) D[k][i] = R(0);
+#pragma unroll
     for (int l = 1; l < Q; l++) {
         const int cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
         const R wl = R(3.0 * wq(l));
         const Mom4<R> jn = mom_site<R>(L, jf, x + cx, y + cy, z + cz);
         const R jv[3] = {jn.x, jn.y, jn.z};
+#pragma unroll
         for (int i = 0; i < 3; i++) {
             D[0][i] += (wl * cx) * jv[i];
             D[1][i] += (wl * cy) * jv[i];

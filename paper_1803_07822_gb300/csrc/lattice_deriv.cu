@@ -125,26 +125,31 @@ __global__ void __launch_bounds__(TBL) k_pad(const __grid_constant__ Box B, cons
     const int x = (int)(s - row * B.ne[0]) - B.pad[0];
     const int y = (int)(row % B.ne[1]) - B.pad[1];
     const int z = (int)(row / B.ne[1]) - B.pad[2];
-    double out;
+    // with sum_{l>0} w_l = 2/3, w = 1/18 on the six faces, 1/36 on the twelve
+    // edges: F = (5/3) f0 - (S_faces + S_edges / 2) / 18
+    double f0, sf = 0.0, se = 0.0;
     if (inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z)) {
-        const double f0 = __ldg(fc + ((long long)z * B.n[1] + y) * B.n[0] + x);
-        double acc = 0.0;
+        f0 = __ldg(fc + ((long long)z * B.n[1] + y) * B.n[0] + x);
         if (order == 4) {
 #pragma unroll
-            for (int l = 1; l < Q; l++)
-                acc += wq(l) * (__ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2))) - f0);
+            for (int l = 1; l < Q; l++) {
+                const double fl = __ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)));
+                if (l <= 6) sf += fl;
+                else se += fl;
+            }
         }
-        out = f0 - acc;
     } else {
-        const double f0 = site(B, fc, order, x, y, z);
-        double acc = 0.0;
+        f0 = site(B, fc, order, x, y, z);
         if (order == 4) {
 #pragma unroll
-            for (int l = 1; l < Q; l++)
-                acc += wq(l) * (site(B, fc, order, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)) - f0);
+            for (int l = 1; l < Q; l++) {
+                const double fl = site(B, fc, order, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2));
+                if (l <= 6) sf += fl;
+                else se += fl;
+            }
         }
-        out = f0 - acc;
     }
+    const double out = order == 4 ? fma(5.0 / 3.0, f0, -fma(0.5, se, sf) * (1.0 / 18.0)) : f0;
     F[(long long)blockIdx.y * B.Ne + s] = out;
 }
 
