@@ -319,7 +319,33 @@ def bench_batch(args):
 ADJOINT_STEPS, ADJOINT_EVERY = 200, 20
 
 
-def adjoint_report(step_kernel):
+def bench_side(args):
+    """One JSON line for the adjoint (adjoint/forward step-time ratio on the
+    adjoint-form channel) or for the lattice gradient of the six metric
+    fields on the 128 x 128 x 256 bench channel (FP64 GFLOP/s)."""
+    import torch
+
+    from paper_1803_07822_gb300.lattice import CurvedLattice
+    torch.cuda.set_device(0)
+    base = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    if args.workload == "adjoint64":
+        r = adjoint_report(args.step_kernel, args.adjoint_steps)
+        line = dict(base, metric="adjoint/forward step-time ratio", value=r["ratio"], unit="ratio",
+                    higher_is_better=False, dtype="f32", ms_per_step=r["backward_ms_per_step"],
+                    config={"workload": r["workload"]}, adjoint=r)
+    else:
+        w = I.dynamic_channel(n=(128, 256, 128), t=500.0)
+        lat = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], storage="fp32")
+        r = lattice_gradient_report(lat, torch.as_tensor(w["chart"].g6, device="cuda"), 4, reps=max(args.steps, 1))
+        line = dict(base, metric="lattice gradient of the metric (App. D, order 4), FP64 GFLOP/s",
+                    value=r["roofline"]["achieved"], unit="GFLOP/s", higher_is_better=True, dtype="f64",
+                    ms_per_step=r["ms"], config={"workload": "six metric fields of the 128x128x256 dynamic channel"},
+                    lattice_gradient=r)
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_report(step_kernel, steps=None):
     """Adjoint/forward step-time ratio on the adjoint-form channel
     (inputs.adjoint_channel: 64 x 128 x 64, 32 deformation coefficients,
     tau 0.8, FP32 storage): the gradient of the streamwise force on the
@@ -340,6 +366,7 @@ def adjoint_report(step_kernel):
     axis = w["layout"][0]
     e3 = [0.0, 0.0, 0.0]
     e3[w["layout"][2]] = 1.0
+    T = ADJOINT_STEPS if steps is None else int(steps)
     lat = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage="fp32",
                         step_kernel=step_kernel)
     c = torch.tensor(w["c"], dtype=torch.float64, device="cuda", requires_grad=True)
@@ -349,14 +376,14 @@ def adjoint_report(step_kernel):
     for rep in range(2):  # the first pass allocates the adjoint workspace and the checkpoints
         torch.cuda.synchronize()
         ev[0].record()
-        J = wall_force_objective(lat, *leaves, ADJOINT_STEPS, ADJOINT_EVERY, axis=axis, side=1, e3=e3)
+        J = wall_force_objective(lat, *leaves, T, ADJOINT_EVERY, axis=axis, side=1, e3=e3)
         ev[1].record()
         grads = torch.autograd.grad(J, leaves)
         ev[2].record()
         torch.cuda.synchronize()
     lat.init_equilibrium()
     ev[3].record()
-    lat.step(ADJOINT_STEPS)
+    lat.step(T)
     ev[4].record()
     torch.autograd.backward(chart, grads, retain_graph=True)  # first call: lazy initialisation in torch
     c.grad = None
@@ -365,10 +392,10 @@ def adjoint_report(step_kernel):
     torch.autograd.backward(chart, grads)
     ev[6].record()
     torch.cuda.synchronize()
-    fwd = ev[3].elapsed_time(ev[4]) / ADJOINT_STEPS
-    bwd = ev[1].elapsed_time(ev[2]) / ADJOINT_STEPS
+    fwd = ev[3].elapsed_time(ev[4]) / T
+    bwd = ev[1].elapsed_time(ev[2]) / T
     sb = lat.state_bytes()
-    mem = lat._adjoint.workspace.numel() + (ADJOINT_STEPS // ADJOINT_EVERY + 1 + ADJOINT_EVERY) * sb
+    mem = lat._adjoint.workspace.numel() + (-(-T // ADJOINT_EVERY) + 1 + min(T, ADJOINT_EVERY)) * sb
     g = c.grad.cpu().numpy()
 
     f64 = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage="fp64",
@@ -380,7 +407,7 @@ def adjoint_report(step_kernel):
         f64.set_metric(g6, dg18)
         f64.set_jacobian(J9)
         f64.init_equilibrium()
-        f64.step(ADJOINT_STEPS)
+        f64.step(T)
         return float(np.dot(e3, f64.wall_force(axis, 1)))
 
     picks, h, fd = [0, 9, 27], 1e-4, []
@@ -393,7 +420,7 @@ def adjoint_report(step_kernel):
     for x in (lat, f64):
         x.close()
     return {"workload": "adjoint-form channel 64x128x64 (span, flow, wall), 32 coefficients, tau 0.8, FP32 storage; "
-                        f"objective: streamwise force on the deformed wall after {ADJOINT_STEPS} steps from rest",
+                        f"objective: streamwise force on the deformed wall after {T} steps from rest",
             "ratio": bwd / fwd, "forward_ms_per_step": fwd, "backward_ms_per_step": bwd,
             "forward_kernel": step_kernel, "checkpoint_every": ADJOINT_EVERY,
             "chart_backward_ms": ev[5].elapsed_time(ev[6]),
@@ -458,7 +485,10 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
-    ap.add_argument("--workload", default="dynamic", choices=["dynamic", "target256", "crop64", "batch64"])
+    ap.add_argument("--workload", default="dynamic",
+                    choices=["dynamic", "target256", "crop64", "batch64", "adjoint64", "lgrad"])
+    ap.add_argument("--adjoint-steps", type=int, default=ADJOINT_STEPS,
+                    help="LBM steps of the adjoint objective (adjoint64 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward step-time ratio")
@@ -473,6 +503,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return bench_batch(args)
+    if args.workload in ("adjoint64", "lgrad"):
+        return bench_side(args)
 
     import torch
 
