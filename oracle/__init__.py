@@ -48,7 +48,8 @@ def _load():
             for name in ("orc_geometry", "orc_init", "orc_step", "orc_fill_boundary",
                          "orc_moments", "orc_mass", "orc_wall_force", "orc_transform",
                          "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
-                         "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian"):
+                         "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian",
+                         "orc_transform_interp"):
                 getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -264,4 +265,17 @@ class Lattice:
                                            _p(self.ginv), _p(sg_new), _p(Jo), _p(Jn),
                                            self._face_ptrs, _p(self.f), _p(self.Fprev)),
                     "transform")
+        self.sqrtg, self.ginv, self.gam = sg_new, gi_new, gam_new
+
+    def transform_interp(self, g6_new, dg18_new, Jold9, Jnew9, psi3):
+        """Chart change with interpolation (Sec. IV.B): every new node takes the
+        old moments at psi3 [3, N] (old lattice coordinates of its point),
+        trilinearly, then transforms them with J~^-1 J(psi) and recomposes."""
+        sg_new, gi_new, gam_new = geometry(self.n, g6_new, dg18_new)
+        Jo = _f64(Jold9, (9, self.N))
+        Jn = _f64(Jnew9, (9, self.N))
+        ps = _f64(psi3, (3, self.N))
+        self._check(self.lib.orc_transform_interp(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv),
+                                                  _p(sg_new), _p(Jo), _p(Jn), _p(ps), self._face_ptrs,
+                                                  _p(self.f), _p(self.Fprev)), "transform_interp")
         self.sqrtg, self.ginv, self.gam = sg_new, gi_new, gam_new

@@ -801,3 +801,101 @@ int orc_lattice_laplacian(const orc_params *p, const double *f, int ncomp, int o
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Chart change with interpolation (Sec. IV.B, transition maps): the   */
+/* new node x~ takes the moments of the old state at x = psi(x~) =     */
+/* h^-1(h~(x~)), off the old grid in general, by trilinear interpolation */
+/* of the moment fields a_(0), a_(1), Pi (or a_(2)) of f and of F(t-1)   */
+/* and of the old Jacobian; then D phi = J~(x~)^-1 J(x), the tensor      */
+/* transformation and the recomposition with the new sqrt(g) as in the   */
+/* node-wise form.  psi3 [3][N] gives x in old lattice coordinates; a    */
+/* periodic axis wraps, a non-periodic one clamps x to [0, n-1].          */
+/* ------------------------------------------------------------------ */
+static void interp_corners(const orc_params *p, const double x[3], long idx8[8], double w8[8])
+{
+    int i0[3], i1[3];
+    double t[3];
+    for (int a = 0; a < 3; a++) {
+        int n = p->n[a];
+        double xa = x[a];
+        int per = p->bc_lo[a] == BC_PERIODIC && p->bc_hi[a] == BC_PERIODIC;
+        if (per) {
+            xa = fmod(xa, (double)n);
+            if (xa < 0) xa += n;
+        } else {
+            if (xa < 0) xa = 0;
+            if (xa > n - 1) xa = n - 1;
+        }
+        double fl = floor(xa);
+        i0[a] = (int)fl;
+        t[a] = xa - fl;
+        if (i0[a] >= n) i0[a] = n - 1; /* xa == n after rounding */
+        i1[a] = per ? (i0[a] + 1) % n : (i0[a] + 1 < n ? i0[a] + 1 : n - 1);
+    }
+    for (int c = 0; c < 8; c++) {
+        int b0 = c & 1, b1 = (c >> 1) & 1, b2 = (c >> 2) & 1;
+        idx8[c] = idx(p, b0 ? i1[0] : i0[0], b1 ? i1[1] : i0[1], b2 ? i1[2] : i0[2]);
+        w8[c] = (b0 ? t[0] : 1 - t[0]) * (b1 ? t[1] : 1 - t[1]) * (b2 ? t[2] : 1 - t[2]);
+    }
+}
+
+int orc_transform_interp(const orc_params *p, const double *sqrtg_old, const double *ginv9_old,
+                         const double *sqrtg_new, const double *Jold9, const double *Jnew9,
+                         const double *psi3, const double *const *uface, double *f, double *Fprev)
+{
+    if (check_params(p)) return -1;
+    long N = nodes(p);
+    double *fb = (double *)malloc(sizeof(double) * Q * N);
+    orc_fill_boundary(p, sqrtg_old, ginv9_old, uface, f, fb);
+    /* moment fields: per source (f, F) a0, a1[3], M[9] */
+    double *mom = (double *)malloc(sizeof(double) * 2 * 13 * N);
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        for (int pass = 0; pass < 2; pass++) {
+            double a0, a1[3], M[3][3];
+            moments(pass ? Fprev : fb, N, v, sqrtg_old[v], &a0, a1, M);
+            if (p->literal_a2)
+                for (int i = 0; i < 3; i++) M[i][i] -= CS2 * a0;
+            double *m = mom + (long)pass * 13 * N;
+            m[v] = a0;
+            for (int i = 0; i < 3; i++) m[(1 + i) * N + v] = a1[i];
+            for (int i = 0; i < 9; i++) m[(4 + i) * N + v] = M[i / 3][i % 3];
+        }
+    }
+#pragma omp parallel for
+    for (long v = 0; v < N; v++) {
+        double x[3] = {psi3[v], psi3[N + v], psi3[2 * N + v]}, w8[8];
+        long i8[8];
+        interp_corners(p, x, i8, w8);
+        double Jo[3][3] = {{0}}, Jn[3][3], Jni[3][3], D[3][3];
+        for (int a = 0; a < 9; a++) {
+            for (int c = 0; c < 8; c++) Jo[a / 3][a % 3] += w8[c] * Jold9[a * N + i8[c]];
+            Jn[a / 3][a % 3] = Jnew9[a * N + v];
+        }
+        inv3(Jn, Jni);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                D[i][j] = 0.0;
+                for (int k = 0; k < 3; k++) D[i][j] += Jni[i][k] * Jo[k][j];
+            }
+        for (int pass = 0; pass < 2; pass++) {
+            const double *m = mom + (long)pass * 13 * N;
+            double a0 = 0.0, a1[3] = {0, 0, 0}, M[3][3] = {{0}};
+            for (int c = 0; c < 8; c++) {
+                a0 += w8[c] * m[i8[c]];
+                for (int i = 0; i < 3; i++) a1[i] += w8[c] * m[(1 + i) * N + i8[c]];
+                for (int i = 0; i < 9; i++) M[i / 3][i % 3] += w8[c] * m[(4 + i) * N + i8[c]];
+            }
+            double t1[3], tM[3][3], t2[3][3];
+            tensor_transform(D, a1, M, t1, tM);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) t2[i][j] = tM[i][j] - (p->literal_a2 ? 0.0 : CS2 * a0 * (i == j));
+            double *dst = pass ? Fprev : f;
+            for (int l = 0; l < Q; l++) dst[l * N + v] = hermite_recompose(l, sqrtg_new[v], a0, t1, t2);
+        }
+    }
+    free(mom);
+    free(fb);
+    return 0;
+}
