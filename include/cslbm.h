@@ -234,6 +234,28 @@ cslbm_status cslbm_adjoint_metric_grad(cslbm_ctx* ctx, const double* g6, const d
                                        double* grad_dg18, double* grad_J9);
 
 /* ---------------------------------------------------------------------------
+ * Chart change with interpolation (Sec. IV.B, transition maps): the new node
+ * x~ takes the old state's moments at x = psi(x~) = h^-1(h~(x~)), generally
+ * off the old grid, by trilinear interpolation of the fields a_(0), a_(1),
+ * Pi (or a_(2)) of f and of the forcing history and of the old Jacobian;
+ * then D phi = J~(x~)^-1 J(x), the tensor transformation and the
+ * recomposition with the new sqrt(g) as in cslbm_update_metric.  A periodic
+ * axis wraps x, a non-periodic one clamps it to [0, n - 1].
+ * ------------------------------------------------------------------------- */
+
+/* Scratch bytes of cslbm_update_metric_interp: 20 values per node at the
+ * compute precision (FP64 for FP64 storage, FP32 otherwise). */
+cslbm_status cslbm_transform_interp_scratch_bytes(const cslbm_ctx* ctx, size_t* bytes);
+
+/* cslbm_update_metric with interpolation.  g6 [6][N], dg18 [18][N], Jnew9
+ * [9][N] as in cslbm_update_metric; psi3 [3][N] the old lattice coordinates
+ * (x, y, z) of the point of every new node.  Every array, scratch included,
+ * is device memory (EINVAL otherwise); ENOMEM for a short scratch; ESTATE
+ * before init_equilibrium.  Asynchronous, like cslbm_update_metric. */
+cslbm_status cslbm_update_metric_interp(cslbm_ctx* ctx, const double* g6, const double* dg18, const double* Jnew9,
+                                        const double* psi3, void* scratch, size_t scratch_bytes);
+
+/* ---------------------------------------------------------------------------
  * Isotropic lattice derivatives (App. D, improved lattice derivatives): with
  * the D3Q19 weights w and velocities c,
  *   G_i f = (1/c_s^2) sum_l w_l c_l^i f(x + c_l)          (order 2)

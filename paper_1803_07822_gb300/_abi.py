@@ -64,6 +64,8 @@ SIGNATURES = {
     "cslbm_step_backward": [_P],
     "cslbm_adjoint_init_backward": [_P],
     "cslbm_adjoint_metric_grad": [_P, _P, _P, _P, _P, _P],
+    "cslbm_transform_interp_scratch_bytes": [_P, ctypes.POINTER(_SZ)],
+    "cslbm_update_metric_interp": [_P, _P, _P, _P, _P, _P, _SZ],
     "cslbm_lattice_gradient_scratch_bytes": [_P, _I, _I, ctypes.POINTER(_SZ)],
     "cslbm_lattice_gradient": [_P, _P, _I, _I, _P, _P, _SZ],
     "cslbm_metric_lattice_scratch_bytes": [_P, _I, ctypes.POINTER(_SZ)],

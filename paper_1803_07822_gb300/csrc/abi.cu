@@ -346,6 +346,42 @@ cslbm_status cslbm_set_metric(cslbm_ctx* c, const double* g6, const double* dg18
     return run_metric(c, g6, dg18, on_device, c->gc, true);
 }
 
+static bool is_device_memory(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cslbm_status cslbm_transform_interp_scratch_bytes(const cslbm_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(CSLBM_EINVAL, "null argument");
+    *bytes = 20 * (size_t)c->N * c->r_bytes;
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_update_metric_interp(cslbm_ctx* c, const double* g6, const double* dg18, const double* Jnew9,
+                                        const double* psi3, void* scratch, size_t scratch_bytes)
+{
+    if (!c || !g6 || !dg18 || !Jnew9 || !psi3) return fail(CSLBM_EINVAL, "null argument");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "update_metric_interp before init_equilibrium");
+    if (!scratch || scratch_bytes < 20 * (size_t)c->N * c->r_bytes) return fail(CSLBM_ENOMEM, "scratch too small");
+    for (const void* q : {(const void*)g6, (const void*)dg18, (const void*)Jnew9, (const void*)psi3, (const void*)scratch})
+        if (!is_device_memory(q)) return fail(CSLBM_EINVAL, "every array of update_metric_interp is device memory");
+    if (cslbm_status s = run_metric(c, g6, dg18, 1, 1 - c->gc, false)) return s;
+    c->ops->transform_interp(c, Jnew9, psi3, scratch);
+    c->launches += 2;
+    LAUNCH_CHECK("interpolating transform kernels");
+    CUDA_TRY(cudaMemcpyAsync(c->J, Jnew9, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->pc ^= 1;
+    c->hc ^= 1;
+    c->gc ^= 1;
+    return CSLBM_OK;
+}
+
 cslbm_status cslbm_set_jacobian(cslbm_ctx* c, const double* J9, int on_device)
 {
     if (!c || !J9) return fail(CSLBM_EINVAL, "null argument");

@@ -88,6 +88,11 @@ struct cslbm_ops {
     // chart change for nodes [v0, v0+cnt): P[pc],H[hc],G[gc] -> P[1-pc],H[1-hc] with G[1-gc]
     void (*transform)(const cslbm_ctx*, const double* Jnew, long long stride, long long v0,
                       long long cnt);
+    // chart change with interpolation: the transformation inputs of every node
+    // into scratch [20][N] (precision R), then every node of P[1-pc],H[1-hc]
+    // from them at psi3 [3][N] (old lattice coordinates) with G[1-gc]; J (old)
+    // is read, not written
+    void (*transform_interp)(const cslbm_ctx*, const double* Jnew, const double* psi3, void* scratch);
     // rho, u (or v) of nodes [v0, v0+cnt) into out arrays with the given stride
     void (*readout)(const cslbm_ctx*, double* rho, double* u3, long long stride, long long v0,
                     long long cnt, int cartesian);

@@ -299,30 +299,79 @@ __global__ void __launch_bounds__(TPB) k_forcing(Lat L, const S* __restrict__ P,
 // the new sqrt(g); the history's A, B, C as scalar, vector, rank-2 tensor.
 // Writes the transformed state into the other buffers (same pull slots).
 // ---------------------------------------------------------------------------
+// The tensor transformation with D phi = Dp and the recomposition with the
+// new sqrt(g) of one node's f-moments (rho, j, M2 = Pi or a_(2)) and history
+// (A, B and Cs = C, or b_(2) = C - c_s^2 delta A with literal), stored into
+// the pull slots and history of node (x, y, z) = v.
 template <class S, class R>
-__global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
-                                                   const R* __restrict__ hin, R* __restrict__ hout,
-                                                   const R* __restrict__ geo_old, const R* __restrict__ geo_new,
-                                                   double* __restrict__ J, const double* __restrict__ Jnew,
-                                                   long long stride, long long v0, long long cnt, int literal)
+__device__ __forceinline__ void transform_store(const Lat& L, S* __restrict__ Pout, R* __restrict__ hout, R sgn,
+                                                int x, int y, int z, long long v, const R (&Dp)[3][3], R rho,
+                                                const R (&j)[3], const R (&M2)[6], R A, const R (&B)[3],
+                                                const R (&Cs)[6], int literal)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    long long v = v0 + t;
-    int x, y, z;
-    node_coords(L, v, x, y, z);
-    const R sgo = geo_old[v];
-    NodeMoments<S, R> M;
-    node_moments<S, R>(L, Pin, hin, geo_old, x, y, z, v, sgo, M);
-    // D phi = Jnew^-1 Jold, in FP64 for FP64 storage and in FP32 otherwise
-    // (the FP64 Jacobians rounded; D phi is stored at the precision of R)
-    using Cm = R;
-    double Jo[9], Jn[9];
+    auto vec = [&](const R in[3], R out[3]) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) {
-        Jo[k] = J[k * L.N + v];
-        Jn[k] = Jnew[k * stride + t];
+        for (int i = 0; i < 3; i++) out[i] = Dp[i][0] * in[0] + Dp[i][1] * in[1] + Dp[i][2] * in[2];
+    };
+    auto ten = [&](const R in[6], R out[6]) {
+        R tmp[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int m = 0; m < 3; m++)
+                tmp[i][m] = Dp[i][0] * in[s6(0, m)] + Dp[i][1] * in[s6(1, m)] + Dp[i][2] * in[s6(2, m)];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = i; k < 3; k++) out[s6(i, k)] = tmp[i][0] * Dp[k][0] + tmp[i][1] * Dp[k][1] + tmp[i][2] * Dp[k][2];
+    };
+    R j2[3], P2[6];
+    vec(j, j2);
+    ten(M2, P2);
+    if (!literal) {
+        P2[0] -= rho * R(1.0 / 3.0);
+        P2[3] -= rho * R(1.0 / 3.0);
+        P2[5] -= rho * R(1.0 / 3.0);
     }
+    // history: A scalar, B vector, C (or, with literal, b_(2) = C - c_s^2 delta A) rank 2
+    Hist<R> Hn;
+    Hn.A = A;
+    vec(B, Hn.B);
+    ten(Cs, Hn.C);
+    if (literal) {
+        Hn.C[0] += Hn.A * R(1.0 / 3.0);
+        Hn.C[3] += Hn.A * R(1.0 / 3.0);
+        Hn.C[5] += Hn.A * R(1.0 / 3.0);
+    }
+    const R isgn = R(1) / sgn;
+    const R trP2 = P2[0] + P2[3] + P2[5];
+    hout[v] = Hn.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) hout[(1 + a) * L.N + v] = Hn.B[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) hout[(4 + a) * L.N + v] = Hn.C[a];
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (r[a] < 0 || r[a] >= L.n[a]) {
+                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
+                else ok = false;
+            }
+        }
+        if (!ok) continue;
+        // f~ - F~/2 - w  with  f~ - w = w/sqrt(g~) [(rho - sqrt g~) + ...]
+        R val = hermite_l(l, isgn, rho - sgn, j2, P2, trP2) - R(0.5) * forcing_l(l, isgn, Hn);
+        Store<S>::st(Pout + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), val);
+    }
+}
+
+// D phi = Jn^-1 Jo at the precision Cm (FP64 for FP64 storage, FP32 otherwise)
+template <class Cm, class R>
+__device__ __forceinline__ void dphi(const double (&Jn)[9], const double (&Jo)[9], R (&Dp)[3][3])
+{
     Cm n[9], o[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -343,7 +392,6 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
         inv[5] = (n[2] * n[3] - n[0] * n[5]) * id;
         inv[8] = (n[0] * n[4] - n[1] * n[3]) * id;
     }
-    R Dp[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -353,76 +401,151 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
             for (int m = 0; m < 3; m++) s += inv[i * 3 + m] * o[m * 3 + k];
             Dp[i][k] = R(s);
         }
+}
+
+// the f-moments and history of a node in the form the transformation takes:
+// out = {rho, j[3], M2[6], A, B[3], Cs[6]}
+template <class S, class R>
+__device__ __forceinline__ void transform_inputs(const Lat& L, const S* __restrict__ Pin, const R* __restrict__ hin,
+                                                 const R* __restrict__ geo_old, int x, int y, int z, long long v,
+                                                 int literal, R (&out)[20])
+{
+    const R sgo = geo_old[v];
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, Pin, hin, geo_old, x, y, z, v, sgo, M);
+    out[0] = M.rho;
 #pragma unroll
-    for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
+    for (int a = 0; a < 3; a++) out[1 + a] = M.j[a];
     // moments of f: a0 = rho, a1 = j, M2 = Pi (or a_(2))
-    R M2[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const bool dia = (k == 0 || k == 3 || k == 5);
-        M2[k] = sgo * ((dia ? R(1.0 / 3.0) : R(0)) + M.m2[k]) + R(0.5) * M.Hp.C[k];
-        if (literal && dia) M2[k] -= M.rho * R(1.0 / 3.0);
+        R m2 = sgo * ((dia ? R(1.0 / 3.0) : R(0)) + M.m2[k]) + R(0.5) * M.Hp.C[k];
+        if (literal && dia) m2 -= M.rho * R(1.0 / 3.0);
+        out[4 + k] = m2;
     }
-    auto vec = [&](const R in[3], R out[3]) {
+    out[10] = M.Hp.A;
 #pragma unroll
-        for (int i = 0; i < 3; i++) out[i] = Dp[i][0] * in[0] + Dp[i][1] * in[1] + Dp[i][2] * in[2];
-    };
-    auto ten = [&](const R in[6], R out[6]) {
-        R tmp[3][3];
+    for (int a = 0; a < 3; a++) out[11 + a] = M.Hp.B[a];
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+    for (int k = 0; k < 6; k++)
+        out[14 + k] = M.Hp.C[k] - ((literal && (k == 0 || k == 3 || k == 5)) ? M.Hp.A * R(1.0 / 3.0) : R(0));
+}
+
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                                   const R* __restrict__ hin, R* __restrict__ hout,
+                                                   const R* __restrict__ geo_old, const R* __restrict__ geo_new,
+                                                   double* __restrict__ J, const double* __restrict__ Jnew,
+                                                   long long stride, long long v0, long long cnt, int literal)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    long long v = v0 + t;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    R in[20];
+    transform_inputs<S, R>(L, Pin, hin, geo_old, x, y, z, v, literal, in);
+    // D phi = Jnew^-1 Jold, in FP64 for FP64 storage and in FP32 otherwise
+    // (the FP64 Jacobians rounded; D phi is stored at the precision of R)
+    double Jo[9], Jn[9];
 #pragma unroll
-            for (int m = 0; m < 3; m++)
-                tmp[i][m] = Dp[i][0] * in[s6(0, m)] + Dp[i][1] * in[s6(1, m)] + Dp[i][2] * in[s6(2, m)];
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int k = i; k < 3; k++) out[s6(i, k)] = tmp[i][0] * Dp[k][0] + tmp[i][1] * Dp[k][1] + tmp[i][2] * Dp[k][2];
-    };
-    R j2[3], P2[6];
-    vec(M.j, j2);
-    ten(M2, P2);
-    if (!literal) {
-        P2[0] -= M.rho * R(1.0 / 3.0);
-        P2[3] -= M.rho * R(1.0 / 3.0);
-        P2[5] -= M.rho * R(1.0 / 3.0);
+    for (int k = 0; k < 9; k++) {
+        Jo[k] = J[k * L.N + v];
+        Jn[k] = Jnew[k * stride + t];
     }
-    // history: A scalar, B vector, C (or, with literal, b_(2) = C - c_s^2 delta A) rank 2
-    Hist<R> Hn;
-    Hn.A = M.Hp.A;
-    vec(M.Hp.B, Hn.B);
-    R Cs[6];
+    R Dp[3][3];
+    dphi<R, R>(Jn, Jo, Dp);
 #pragma unroll
-    for (int k = 0; k < 6; k++) Cs[k] = M.Hp.C[k] - ((literal && (k == 0 || k == 3 || k == 5)) ? M.Hp.A * R(1.0 / 3.0) : R(0));
-    ten(Cs, Hn.C);
-    if (literal) {
-        Hn.C[0] += Hn.A * R(1.0 / 3.0);
-        Hn.C[3] += Hn.A * R(1.0 / 3.0);
-        Hn.C[5] += Hn.A * R(1.0 / 3.0);
+    for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
+    const R j[3] = {in[1], in[2], in[3]}, B[3] = {in[11], in[12], in[13]};
+    const R M2[6] = {in[4], in[5], in[6], in[7], in[8], in[9]};
+    const R Cs[6] = {in[14], in[15], in[16], in[17], in[18], in[19]};
+    transform_store<S, R>(L, Pout, hout, geo_new[v], x, y, z, v, Dp, in[0], j, M2, in[10], B, Cs, literal);
+}
+
+// Chart change with interpolation, pass 1: the transformation inputs of every
+// old node into mf [20][N]
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_moment_fields(Lat L, const S* __restrict__ Pin, const R* __restrict__ hin,
+                                                       const R* __restrict__ geo_old, R* __restrict__ mf, int literal)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    R in[20];
+    transform_inputs<S, R>(L, Pin, hin, geo_old, x, y, z, v, literal, in);
+#pragma unroll
+    for (int k = 0; k < 20; k++) mf[k * L.N + v] = in[k];
+}
+
+// trilinear corners of the point p (old lattice coordinates) along one axis:
+// a periodic axis wraps, a non-periodic one clamps p to [0, n - 1]
+__device__ __forceinline__ void interp_axis(double p, int n, bool per, int& i0, int& i1, double& t)
+{
+    if (per) {
+        p = fmod(p, (double)n);
+        if (p < 0.0) p += n;
+    } else {
+        p = fmin(fmax(p, 0.0), (double)(n - 1));
     }
-    const R sgn = geo_new[v], isgn = R(1) / sgn;
-    const R trP2 = P2[0] + P2[3] + P2[5];
-    hout[v] = Hn.A;
+    const double fl = floor(p);
+    i0 = (int)fl;
+    t = p - fl;
+    if (i0 >= n) i0 = n - 1;
+    i1 = per ? (i0 + 1 == n ? 0 : i0 + 1) : (i0 + 1 < n ? i0 + 1 : n - 1);
+}
+
+// pass 2: every new node from the fields at psi(x~) = psi3[.][v]
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_transform_interp(Lat L, S* __restrict__ Pout, R* __restrict__ hout,
+                                                          const R* __restrict__ geo_new, const double* __restrict__ J,
+                                                          const double* __restrict__ Jnew,
+                                                          const double* __restrict__ psi, const R* __restrict__ mf,
+                                                          int literal)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    int c0[3], c1[3];
+    double t[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) hout[(1 + a) * L.N + v] = Hn.B[a];
+    for (int a = 0; a < 3; a++)
+        interp_axis(psi[a * L.N + v], L.n[a], L.bclo[a] == BC_PERIODIC && L.bchi[a] == BC_PERIODIC, c0[a], c1[a],
+                    t[a]);
+    long long ix[8];
+    double w[8];
 #pragma unroll
-    for (int a = 0; a < 6; a++) hout[(4 + a) * L.N + v] = Hn.C[a];
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
-        bool ok = true;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (r[a] < 0 || r[a] >= L.n[a]) {
-                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
-                else ok = false;
-            }
-        }
-        if (!ok) continue;
-        // f~ - F~/2 - w  with  f~ - w = w/sqrt(g~) [(rho - sqrt g~) + ...]
-        R val = hermite_l(l, isgn, M.rho - sgn, j2, P2, trP2) - R(0.5) * forcing_l(l, isgn, Hn);
-        Store<S>::st(Pout + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), val);
+    for (int c = 0; c < 8; c++) {
+        const int b0 = c & 1, b1 = (c >> 1) & 1, b2 = (c >> 2) & 1;
+        ix[c] = nidx(L, b0 ? c1[0] : c0[0], b1 ? c1[1] : c0[1], b2 ? c1[2] : c0[2]);
+        w[c] = (b0 ? t[0] : 1.0 - t[0]) * (b1 ? t[1] : 1.0 - t[1]) * (b2 ? t[2] : 1.0 - t[2]);
     }
+    double Jo[9], Jn[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; c++) s += w[c] * J[k * L.N + ix[c]];
+        Jo[k] = s;
+        Jn[k] = Jnew[k * L.N + v];
+    }
+    R Dp[3][3];
+    dphi<R, R>(Jn, Jo, Dp);
+    R in[20];
+#pragma unroll
+    for (int k = 0; k < 20; k++) {
+        R s = R(0);
+#pragma unroll
+        for (int c = 0; c < 8; c++) s += R(w[c]) * mf[k * L.N + ix[c]];
+        in[k] = s;
+    }
+    const R j[3] = {in[1], in[2], in[3]}, B[3] = {in[11], in[12], in[13]};
+    const R M2[6] = {in[4], in[5], in[6], in[7], in[8], in[9]};
+    const R Cs[6] = {in[14], in[15], in[16], in[17], in[18], in[19]};
+    transform_store<S, R>(L, Pout, hout, geo_new[v], x, y, z, v, Dp, in[0], j, M2, in[10], B, Cs, literal);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,6 +738,15 @@ template <class S, class R> struct Launch {
                                                                H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, Jnew,
                                                                stride, v0, cnt, c->p.transform_flags & 1);
     }
+    static void transform_interp(const cslbm_ctx* c, const double* Jnew, const double* psi3, void* scratch)
+    {
+        const int lit = c->p.transform_flags & 1;
+        k_moment_fields<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                                   (R*)scratch, lit);
+        k_transform_interp<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, 1 - c->pc), H(c, 1 - c->hc),
+                                                                      G(c, 1 - c->gc), c->J, Jnew, psi3,
+                                                                      (const R*)scratch, lit);
+    }
     static void readout(const cslbm_ctx* c, double* rho, double* u3, long long stride, long long v0, long long cnt,
                         int cartesian)
     {
@@ -640,7 +772,7 @@ template <class S, class R> struct Launch {
     static constexpr cslbm_ops ops()
     {
         return cslbm_ops{&metric, &init_scatter, &momentum_field, &step, &half_shift,
-                         &transform, &readout, &mass, &wall_force, &check};
+                         &transform, &transform_interp, &readout, &mass, &wall_force, &check};
     }
 };
 

@@ -284,6 +284,70 @@ def adjoint_channel(n=(64, 128, 64), kmax=8, lmax=3, seed=5000, tau=0.8, shrink=
                 bc_hi=base["bc_hi"], fext=base["fext"], layout=layout)
 
 
+def tg_chart(n, t, eps=0.1, eta=0.05):
+    """Periodic, separable, time-dependent chart of the Taylor-Green study:
+    x_c^i = x^i - eps (L_i / 2 pi) cos(2 pi x^i / L_i - eta t) on the two
+    in-plane axes (0, 1), the identity on axis 2; so J^i_i = 1 + eps sin(2 pi
+    x^i / L_i - eta t) and g = diag(J00^2, J11^2, 1)."""
+    r = grid(n)
+    N = r[0].size
+    J9 = np.zeros((9, N))
+    hess = np.zeros((27, N))
+    J9[8] = 1.0
+    for a in (0, 1):
+        k = 2 * np.pi / n[a]
+        th = k * r[a] - eta * t
+        J9[a * 3 + a] = 1.0 + eps * np.sin(th)
+        hess[a * 9 + a * 3 + a] = eps * k * np.cos(th)
+    return Chart(tuple(n), J9, hess)
+
+
+def tg_position(n, t, eps=0.1, eta=0.05):
+    """Cartesian positions x_c [3, N] of the nodes under tg_chart at time t."""
+    r = grid(n)
+    out = np.stack(r).astype(np.float64)
+    for a in (0, 1):
+        L = n[a]
+        out[a] = r[a] - eps * (L / (2 * np.pi)) * np.cos(2 * np.pi * r[a] / L - eta * t)
+    return out
+
+
+def tg_psi(n, t_old, t_new, eps=0.1, eta=0.05):
+    """Transition map psi = h_old^-1(h_new(x~)) [3, N] of tg_chart from t_old to
+    t_new: per in-plane axis the solution x of x - eps (L/2pi) cos(2 pi x/L -
+    eta t_old) = x_c(x~, t_new), by Newton's method (the map is monotone for
+    eps < 1)."""
+    xc = tg_position(n, t_new, eps, eta)
+    r = grid(n)
+    psi = np.stack(r).astype(np.float64)
+    for a in (0, 1):
+        L = n[a]
+        k = 2 * np.pi / L
+        x = xc[a].copy()
+        for _ in range(50):
+            fx = x - eps / k * np.cos(k * x - eta * t_old) - xc[a]
+            dx = fx / (1.0 + eps * np.sin(k * x - eta * t_old))
+            x -= dx
+            if np.abs(dx).max() < 1e-14:
+                break
+        psi[a] = x
+    return psi
+
+
+def tg_velocity(xc, L, v0, nu, t):
+    """The decaying 2D Taylor-Green field at Cartesian points xc [3, N]:
+    v = v0 exp(-2 nu k^2 t) (sin kx cos ky, -cos kx sin ky, 0), k = 2 pi / L,
+    and the density 1 - (v0^2 e^{-4 nu k^2 t} / (4 c_s^2)) (cos 2kx + cos 2ky)
+    of its pressure."""
+    k = 2 * np.pi / L
+    d = np.exp(-2 * nu * k * k * t)
+    v = np.zeros_like(xc)
+    v[0] = v0 * d * np.sin(k * xc[0]) * np.cos(k * xc[1])
+    v[1] = -v0 * d * np.cos(k * xc[0]) * np.sin(k * xc[1])
+    rho = 1.0 - (v0 * d) ** 2 * 3.0 / 4.0 * (np.cos(2 * k * xc[0]) + np.cos(2 * k * xc[1]))
+    return rho, v
+
+
 def plain_fp64_channel(n=(16, 32, 16), layout=LAYOUT):
     """Static one-mode channel (16 x 16 x 32 nodes, 32 along the flow):
     d = 0.05 H sin(2 pi s / n_flow), tau = 0.8, body force for umax = 0.05."""

@@ -99,6 +99,21 @@ class CurvedLattice:
             raise ValueError("metric inputs must all be host or all device arrays")
         call("cslbm_update_metric", self.ctx, p1, p2, p3, d1)
 
+    def update_metric_interp(self, g6, dg18, J9, psi3):
+        """Chart change with interpolation: every new node takes the old
+        state's moments at psi3 [3, N] (old lattice coordinates of its point)."""
+        torch = _torch()
+        g = self._dev64(g6, 6)
+        d = self._dev64(dg18, 18)
+        J = self._dev64(J9, 9)
+        ps = self._dev64(psi3, 3)
+        nb = ctypes.c_size_t(0)
+        call("cslbm_transform_interp_scratch_bytes", self.ctx, ctypes.byref(nb))
+        scratch = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        call("cslbm_update_metric_interp", self.ctx, g.data_ptr(), d.data_ptr(), J.data_ptr(), ps.data_ptr(),
+             scratch.data_ptr(), scratch.numel())
+        self._keep = (g, d, J, ps, scratch)  # alive until the stream has used them
+
     # -- lattice derivatives (App. D) ----------------------------------------
     def _dev64(self, a, rows):
         torch = _torch()
