@@ -462,6 +462,40 @@ def lattice_gradient_report(lat, g6, order=4, reps=5):
                          "frac": gf / FP64_PEAK_GFLOPS, "peak_kind": "derived from unit counts and clock"}}
 
 
+def transform_interp_report(lat, dev, layout, reps=5):
+    """Device time of one chart change of the bench channel (metric kernel +
+    transformation) with the interpolating form against the node-wise one.
+    The transition map of the channel chart h^w = x_w (1 + d/H) between two
+    snapshots: x_w = x~_w J~^w_w / J^w_w (J^w_w = 1 + d/H), the rest fixed."""
+    import torch
+    w = layout[0]
+    grid = torch.as_tensor(np.stack(I.grid(lat.n)), device="cuda")
+    pairs = [(dev[i], dev[i + 1]) for i in range(len(dev) - 1)]
+    psis = []
+    for a, b in pairs:
+        psi = grid.clone()
+        psi[w] = psi[w] * b["J9"][w * 3 + w] / a["J9"][w * 3 + w]
+        psis.append(psi)
+    out = {}
+    for mode in ("node", "interp"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(reps + 2):
+            if rep == 2:
+                e0.record()
+            for (a, b), psi in zip(pairs, psis):
+                if mode == "interp":
+                    lat.update_metric_interp(b["g6"], b["dg18"], b["J9"], psi)
+                else:
+                    lat.update_metric(b["g6"], b["dg18"], b["J9"])
+                lat.set_jacobian(a["J9"])  # back to the pair's old chart for the next change
+        e1.record()
+        torch.cuda.synchronize()
+        out[mode] = e0.elapsed_time(e1) / (reps * len(pairs))
+    return {"node_wise_ms": out["node"], "interp_ms": out["interp"], "nodes": lat.N,
+            "note": "one chart change incl. the metric kernel; the interpolating form adds the moment-field pass "
+                    "and reads 8 corners per node (20 fields + the FP64 Jacobian)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -598,6 +632,7 @@ def main():
     }
     if rank == 0 and world == 1:
         line["lattice_gradient"] = lattice_gradient_report(lat, dev[0]["g6"])
+        line["transform_interp"] = transform_interp_report(lat, dev, w["layout"])
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
