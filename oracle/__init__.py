@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cslbm_oracle.c")
+_SRC2D = os.path.join(_HERE, "cslbm_oracle2d.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -31,10 +32,11 @@ PERIODIC, WALL, INFLOW, OUTFLOW = 0, 1, 2, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off, so x86 and Arm agree)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC2D))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+               "-ffp-contract=off", _SRC, _SRC2D, "-o", tmp, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -49,7 +51,8 @@ def _load():
                          "orc_moments", "orc_mass", "orc_wall_force", "orc_transform",
                          "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
                          "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian",
-                         "orc_transform_interp"):
+                         "orc_transform_interp", "o2_lattice", "o2_geometry", "o2_init", "o2_step",
+                         "o2_moments", "o2_mass", "o2_wall_force", "o2_transform"):
                 getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -279,3 +282,102 @@ class Lattice:
                                                   _p(sg_new), _p(Jo), _p(Jn), _p(ps), self._face_ptrs,
                                                   _p(self.f), _p(self.Fprev)), "transform_interp")
         self.sqrtg, self.ginv, self.gam = sg_new, gi_new, gam_new
+
+
+# ---------------------------------------------------------------------------
+# two dimensions (D2Q9), cslbm_oracle2d.c
+# ---------------------------------------------------------------------------
+class _Params2(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 2), ("bc_lo", ctypes.c_int * 2), ("bc_hi", ctypes.c_int * 2),
+                ("tau", ctypes.c_double), ("theta", ctypes.c_double), ("fext", ctypes.c_double * 2)]
+
+
+def lattice2d():
+    """(c [9,2] int, w [9]) of the D2Q9 oracle."""
+    c = np.zeros(18, dtype=np.int32)
+    w = np.zeros(9)
+    _load().o2_lattice(_p(c), _p(w))
+    return c.reshape(9, 2), w
+
+
+def geometry2d(n, g3, dg6):
+    """g_ij [3, N], d_k g_ij [6, N] -> (sqrt g [N], g^ij [4, N], Gamma^i_jk [8, N])."""
+    N = int(np.prod(n))
+    g3, dg6 = _f64(g3, (3, N)), _f64(dg6, (6, N))
+    sg, gi, gam = np.zeros(N), np.zeros((4, N)), np.zeros((8, N))
+    if _load().o2_geometry((ctypes.c_int * 2)(*n), _p(g3), _p(dg6), _p(sg), _p(gi), _p(gam)):
+        raise ValueError("metric not positive definite")
+    return sg, gi, gam
+
+
+class Lattice2D:
+    """The D2Q9 oracle: literal f-form, FP64, n = (n0, n1), bc per axis."""
+
+    def __init__(self, n, bc_lo=(0, 0), bc_hi=None, tau=0.8, theta=1.0 / 3.0, fext=(0.0, 0.0)):
+        self.lib = _load()
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        bc_hi = bc_lo if bc_hi is None else bc_hi
+        self.params = _Params2((ctypes.c_int * 2)(*self.n), (ctypes.c_int * 2)(*bc_lo), (ctypes.c_int * 2)(*bc_hi),
+                               float(tau), float(theta), (ctypes.c_double * 2)(*fext))
+        self.f = np.zeros((9, self.N))
+        self.Fprev = np.zeros((9, self.N))
+        self.sqrtg = np.ones(self.N)
+        self.ginv = np.zeros((4, self.N))
+        self.ginv[[0, 3]] = 1.0
+        self.gam = np.zeros((8, self.N))
+        self._faces = [None] * 4
+        self._face_ptrs = (ctypes.c_void_p * 4)()
+
+    def set_metric(self, g3, dg6):
+        self.sqrtg, self.ginv, self.gam = geometry2d(self.n, g3, dg6)
+
+    def set_face_velocity(self, axis, side, u2):
+        k = axis * 2 + side
+        if u2 is None:
+            self._faces[k], self._face_ptrs[k] = None, None
+        else:
+            a = _f64(u2, (2, self.n[1 - axis]))
+            self._faces[k] = a
+            self._face_ptrs[k] = a.ctypes.data
+
+    def _check(self, rc, what):
+        if rc:
+            raise ValueError(f"oracle {what} failed")
+
+    def init(self, rho0=None, u0=None):
+        rho0 = np.ones(self.N) if rho0 is None else _f64(rho0, (self.N,))
+        u0 = np.zeros((2, self.N)) if u0 is None else _f64(u0, (2, self.N))
+        self._check(self.lib.o2_init(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), _p(self.gam), _p(rho0),
+                                     _p(u0), self._face_ptrs, _p(self.f), _p(self.Fprev)), "init")
+
+    def step(self, nsteps=1):
+        self._check(self.lib.o2_step(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), _p(self.gam),
+                                     self._face_ptrs, _p(self.f), _p(self.Fprev), int(nsteps)), "step")
+
+    def moments(self, J4=None):
+        rho, u = np.zeros(self.N), np.zeros((2, self.N))
+        Jk = None if J4 is None else _f64(J4, (4, self.N))
+        self._check(self.lib.o2_moments(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), self._face_ptrs,
+                                        _p(self.f), None if Jk is None else _p(Jk), _p(rho), _p(u)), "moments")
+        return rho, u
+
+    def mass(self):
+        out = ctypes.c_double(0.0)
+        self._check(self.lib.o2_mass(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), self._face_ptrs,
+                                     _p(self.f), ctypes.byref(out)), "mass")
+        return out.value
+
+    def wall_force(self, axis, side, J4):
+        out = np.zeros(2)
+        Jk = _f64(J4, (4, self.N))
+        self._check(self.lib.o2_wall_force(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), self._face_ptrs,
+                                           _p(self.f), _p(Jk), int(axis), int(side), _p(out)), "wall force")
+        return out
+
+    def transform(self, g3_new, dg6_new, Jold4, Jnew4):
+        sg, gi, gam = geometry2d(self.n, g3_new, dg6_new)
+        Jo, Jn = _f64(Jold4, (4, self.N)), _f64(Jnew4, (4, self.N))
+        self._check(self.lib.o2_transform(ctypes.byref(self.params), _p(self.sqrtg), _p(self.ginv), _p(sg), _p(Jo),
+                                          _p(Jn), self._face_ptrs, _p(self.f), _p(self.Fprev)), "transform")
+        self.sqrtg, self.ginv, self.gam = sg, gi, gam

@@ -348,6 +348,95 @@ def tg_velocity(xc, L, v0, nu, t):
     return rho, v
 
 
+# ---------------------------------------------------------------------------
+# two dimensions (D2Q9): node = x + n0 y; g3 = (g00, g01, g11); dg6 = d_k g_ij
+# at (k * 3 + ij); J4 = J^a_i at (a * 2 + i)
+# ---------------------------------------------------------------------------
+@dataclass
+class Chart2D:
+    n: tuple
+    J4: np.ndarray    # [4, N]
+    hess: np.ndarray  # [8, N] d_j d_k h^a at (a * 4 + j * 2 + k)
+
+    @property
+    def g3(self):
+        J = self.J4.reshape(2, 2, -1)
+        g = np.einsum("ain,ajn->ijn", J, J)
+        return np.stack([g[0, 0], g[0, 1], g[1, 1]])
+
+    @property
+    def dg6(self):
+        J = self.J4.reshape(2, 2, -1)
+        Hs = self.hess.reshape(2, 2, 2, -1)  # [a, j, k]
+        dg = np.einsum("akin,ajn->kijn", Hs, J) + np.einsum("ain,akjn->kijn", J, Hs)
+        return np.stack([dg[k, i, j] for k in range(2) for i, j in ((0, 0), (0, 1), (1, 1))])
+
+
+def grid2d(n):
+    y, x = np.meshgrid(np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return x.ravel().astype(np.float64), y.ravel().astype(np.float64)
+
+
+def channel_chart2d(n, d, dd, ddd):
+    """Exterior chart of a 2-D channel whose top wall (y = H = n1 - 1) is
+    displaced by d(x): h^x = x, h^y = y (1 + d(x)/H); d, d', d'' per node."""
+    x, y = grid2d(n)
+    H = n[1] - 1
+    N = x.size
+    J4 = np.zeros((4, N))
+    J4[0] = 1.0
+    J4[2] = y * dd / H
+    J4[3] = 1.0 + d / H
+    hess = np.zeros((8, N))
+    hess[4 + 0] = y * ddd / H      # d_x d_x h^y
+    hess[4 + 1] = dd / H           # d_x d_y h^y
+    hess[4 + 2] = dd / H           # d_y d_x h^y
+    return Chart2D(tuple(n), J4, hess)
+
+
+def flat_chart2d(n):
+    N = int(np.prod(n))
+    J4 = np.zeros((4, N))
+    J4[[0, 3]] = 1.0
+    return Chart2D(tuple(n), J4, np.zeros((8, N)))
+
+
+def reparam_chart2d(n, eps):
+    """Flat channel reparametrised across the walls (axis 1): y_c = y + eps (L/pi) sin(pi y / L), L = n1 - 1."""
+    x, y = grid2d(n)
+    L = n[1] - 1
+    N = x.size
+    J4 = np.zeros((4, N))
+    J4[0] = 1.0
+    J4[3] = 1.0 + eps * np.cos(np.pi * y / L)
+    hess = np.zeros((8, N))
+    hess[4 + 3] = -eps * np.pi / L * np.sin(np.pi * y / L)
+    return Chart2D(tuple(n), J4, hess)
+
+
+def flag_channel(n=(257, 65), amp=0.05, width=0.15, center=0.35, re=100.0, tau=0.6):
+    """2-D flag-like channel: walls at y = 0 and y = H, a parabolic inlet at x
+    = 0 (centre-line speed from Re = U H / nu), an outlet at x = n0 - 1, the top
+    wall indented by a Gaussian bump d(x) = -amp H exp(-((x - c L)/(w L))^2 / 2)
+    (a concavity, the shape of the paper's stability study).  Returns a dict
+    with the chart, bcs (1 wall, 2 inflow, 3 outflow) and the inlet velocity
+    (contravariant, [2, n1])."""
+    x, y = grid2d(n)
+    L, H = n[0] - 1, n[1] - 1
+    xs = (x - center * L) / (width * L)
+    g = np.exp(-0.5 * xs * xs)
+    d = -amp * H * g
+    dd = amp * H * g * xs / (width * L)
+    ddd = amp * H * g * (1.0 - xs * xs) / (width * L) ** 2
+    ch = channel_chart2d(n, d, dd, ddd)
+    nu = (tau - 0.5) / 3.0
+    U = re * nu / H
+    yy = np.arange(n[1], dtype=np.float64)
+    u_in = np.zeros((2, n[1]))
+    u_in[0] = 4.0 * U * yy * (H - yy) / (H * H)  # the inlet column has d = 0 there (J = identity)
+    return dict(n=tuple(n), chart=ch, bc_lo=(2, 1), bc_hi=(3, 1), tau=tau, u_in=u_in, umax=U)
+
+
 def plain_fp64_channel(n=(16, 32, 16), layout=LAYOUT):
     """Static one-mode channel (16 x 16 x 32 nodes, 32 along the flow):
     d = 0.05 H sin(2 pi s / n_flow), tau = 0.8, body force for umax = 0.05."""

@@ -1,0 +1,119 @@
+"""Pins of the two-dimensional (D2Q9) oracle against what the method fixes:
+the flat metric reduces it to textbook D2Q9 BGK; rest stays at rest and mass
+is conserved; plane Poiseuille flow between walls on the nodes; the same flow
+under a re-parametrised (curved) metric converges to the analytic Cartesian
+profile; the wall force at rest is pressure times length; a chart change to
+the same chart leaves the moments."""
+import numpy as np
+
+import oracle
+from paper_1803_07822_gb300 import inputs as I
+
+P, W = 0, 1
+
+
+def textbook_d2q9(f, tau, steps, n):
+    """Plain D2Q9 BGK, periodic, pull streaming: f_eq = w rho (1 + 3 c.u +
+    9/2 (c.u)^2 - 3/2 u^2)."""
+    c, w = oracle.lattice2d()
+    f = f.reshape(9, n[1], n[0]).copy()
+    for _ in range(steps):
+        rho = f.sum(0)
+        u = np.einsum("la,lyx->ayx", c.astype(float), f) / rho
+        cu = np.einsum("la,ayx->lyx", c.astype(float), u)
+        feq = w[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u * u).sum(0))
+        fs = f - (f - feq) / tau
+        f = np.stack([np.roll(np.roll(fs[l], c[l, 1], axis=0), c[l, 0], axis=1) for l in range(9)])
+    return f.reshape(9, -1)
+
+
+def test_flat_periodic_is_textbook_bgk():
+    n = (12, 10)
+    x, y = I.grid2d(n)
+    rho0 = 1.0 + 0.02 * np.sin(2 * np.pi * x / n[0])
+    u0 = np.stack([0.03 * np.cos(2 * np.pi * y / n[1]), 0.01 * np.sin(2 * np.pi * x / n[0])])
+    o = oracle.Lattice2D(n, (P, P), (P, P), tau=0.7)
+    ch = I.flat_chart2d(n)
+    o.set_metric(ch.g3, ch.dg6)
+    o.init(rho0, u0)
+    f0 = o.f.copy()
+    o.step(40)
+    ref = textbook_d2q9(f0, 0.7, 40, n)
+    assert np.abs(o.f - ref).max() < 1e-13
+
+
+def test_rest_and_mass():
+    n = (9, 7)
+    ch = I.flat_chart2d(n)
+    o = oracle.Lattice2D(n, (P, W), (P, W), tau=0.8)
+    o.set_metric(ch.g3, ch.dg6)
+    o.init()
+    m0 = o.mass()
+    o.step(50)
+    r, u = o.moments()
+    assert np.abs(u).max() < 1e-15 and np.abs(r - 1).max() < 1e-14
+    x, y = I.grid2d((8, 8))
+    o = oracle.Lattice2D((8, 8), (P, P), (P, P), tau=0.8)
+    ch = I.flat_chart2d((8, 8))
+    o.set_metric(ch.g3, ch.dg6)
+    o.init(1 + 0.05 * np.cos(2 * np.pi * x / 8), np.stack([0.02 + 0 * x, 0 * x]))
+    m0 = o.mass()
+    o.step(100)
+    assert abs(o.mass() - m0) < 1e-12 * m0
+
+
+def poiseuille(n1, eps, tau=1.0, umax=0.02):
+    """Plane Poiseuille flow between walls on the nodes y = 0, L (L = n1 - 1),
+    driven by F = 8 nu umax / L^2 along x, under the chart y_c = y + eps (L/pi)
+    sin(pi y/L); relative L2 error of the Cartesian velocity at the nodes'
+    positions against F y_c (L - y_c) / (2 nu rho)."""
+    n = (4, n1)
+    L = n1 - 1
+    nu = (tau - 0.5) / 3.0
+    F = 8.0 * nu * umax / L ** 2
+    ch = I.reparam_chart2d(n, eps)
+    o = oracle.Lattice2D(n, (P, W), (P, W), tau=tau, fext=(F, 0.0))
+    o.set_metric(ch.g3, ch.dg6)
+    o.init()
+    o.step(int(6 * L ** 2 / nu))
+    r, v = o.moments(ch.J4)
+    y = I.grid2d(n)[1]
+    yc = y + eps * (L / np.pi) * np.sin(np.pi * y / L)
+    exact = F * yc * (L - yc) / (2.0 * nu * r.mean())
+    return np.linalg.norm(v[0] - exact) / np.linalg.norm(exact), v
+
+
+def test_flat_poiseuille_matches_analytic():
+    err, v = poiseuille(17, 0.0)
+    assert err < 1e-3
+    assert np.abs(v[1]).max() < 1e-14
+
+
+def test_reparametrised_poiseuille_converges_at_second_order():
+    errs = [poiseuille(n1, 0.1)[0] for n1 in (9, 17, 33)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.7), (errs, rates)
+
+
+def test_wall_force_at_rest_is_pressure_times_length():
+    n = (10, 8)
+    for ch in (I.flat_chart2d(n), I.channel_chart2d(n, *[np.full(80, v) for v in (0.3, 0.0, 0.0)])):
+        o = oracle.Lattice2D(n, (P, W), (P, W), tau=0.8)
+        o.set_metric(ch.g3, ch.dg6)
+        o.init()
+        F = o.wall_force(1, 1, ch.J4)
+        assert abs(F[1] - n[0] / 3.0) < 1e-12 and abs(F[0]) < 1e-14
+
+
+def test_transform_to_the_same_chart_keeps_the_moments():
+    w = I.flag_channel((40, 17), amp=0.05)
+    ch = w["chart"]
+    o = oracle.Lattice2D(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"])
+    o.set_metric(ch.g3, ch.dg6)
+    o.set_face_velocity(0, 0, w["u_in"])
+    o.init()
+    o.step(30)
+    r0, u0 = o.moments(ch.J4)
+    o.transform(ch.g3, ch.dg6, ch.J4, ch.J4)
+    r1, u1 = o.moments(ch.J4)
+    assert np.abs(r1 - r0).max() < 1e-14 and np.abs(u1 - u0).max() < 1e-14
