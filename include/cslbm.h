@@ -329,6 +329,49 @@ cslbm_status cslbm_batch_tune(cslbm_batch* b, int reps, int* block_nodes, float*
 cslbm_status cslbm_batch_launches(const cslbm_batch* b, long long* launches);
 cslbm_status cslbm_batch_destroy(cslbm_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Two dimensions (D2Q9): the same method on the nine-velocity square lattice
+ * (the paper's 2-D flag simulations).  Node v = x + n0 y; FP64 inputs
+ * g3 [3][N] = g00, g01, g11, dg6 [6][N] = d_k g_ij at (k * 3 + ij), J4 [4][N]
+ * = J^a_i at (a * 2 + i); face velocity of face (axis, side) [2][n of the
+ * other axis], contravariant.  Storage and arithmetic FP32 or FP64.  Same
+ * ownership and error conventions as above; on_device = 0 means host arrays
+ * (staged through the workspace, synchronising).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n[2];             /* nodes along axes 0 and 1 */
+    int bc_lo[2], bc_hi[2];
+    double tau, theta;    /* theta <= 0: 1/3 */
+    double fext[2];       /* body force density, contravariant */
+    int storage;          /* CSLBM_FP32 or CSLBM_FP64 */
+} cslbm2d_params;
+typedef struct cslbm2d_ctx cslbm2d_ctx;
+
+cslbm_status cslbm2d_workspace_bytes(const cslbm2d_params* p, size_t* bytes);
+cslbm_status cslbm2d_create(const cslbm2d_params* p, void* workspace, size_t bytes, void* stream, cslbm2d_ctx** out);
+cslbm_status cslbm2d_destroy(cslbm2d_ctx* ctx);
+/* geometry (App. A in 2-D: g^ij, sqrt(g), Gamma) from g and dg; EINVAL when g
+ * is not positive definite somewhere (synchronises) */
+cslbm_status cslbm2d_set_metric(cslbm2d_ctx* ctx, const double* g3, const double* dg6, int on_device);
+cslbm_status cslbm2d_set_jacobian(cslbm2d_ctx* ctx, const double* J4, int on_device);
+/* chart change: new geometry and the node-wise transformation of f and of
+ * the forcing history (Sec. IV.B) */
+cslbm_status cslbm2d_update_metric(cslbm2d_ctx* ctx, const double* g3, const double* dg6, const double* Jnew4,
+                                   int on_device);
+cslbm_status cslbm2d_set_boundary_velocity(cslbm2d_ctx* ctx, int axis, int side, const double* u2, int on_device);
+/* f = f^eq(rho, u; g), F(-dt) := F(0); rho [N] and u2 [2][N] (contravariant)
+ * may be null for 1 and 0 */
+cslbm_status cslbm2d_init_equilibrium(cslbm2d_ctx* ctx, const double* rho, const double* u2, int on_device);
+/* nsteps LBM steps (two kernels each), asynchronous */
+cslbm_status cslbm2d_step(cslbm2d_ctx* ctx, int nsteps);
+/* rho [N], u2 [2][N] (contravariant, or Cartesian v = J u) of the state with
+ * the boundary rule applied; synchronises */
+cslbm_status cslbm2d_get_moments(cslbm2d_ctx* ctx, double* rho, double* u2, int cartesian, int on_device);
+/* FP64 sum of sqrt(g) rho; synchronises */
+cslbm_status cslbm2d_total_mass(cslbm2d_ctx* ctx, double* out);
+/* force of the fluid on face (axis, side), s sum J T^{i axis} sqrt(g) per unit depth, FP64; synchronises */
+cslbm_status cslbm2d_wall_force(cslbm2d_ctx* ctx, int axis, int side, double out2[2]);
+
 const char* cslbm_last_error(void);
 
 #ifdef __cplusplus

@@ -32,6 +32,12 @@ class Params(ctypes.Structure):
                 ("step_kernel", ctypes.c_int)]
 
 
+class Params2D(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 2), ("bc_lo", ctypes.c_int * 2), ("bc_hi", ctypes.c_int * 2),
+                ("tau", ctypes.c_double), ("theta", ctypes.c_double), ("fext", ctypes.c_double * 2),
+                ("storage", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _SZ = ctypes.c_size_t
@@ -78,6 +84,18 @@ SIGNATURES = {
     "cslbm_batch_tune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)],
     "cslbm_batch_launches": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "cslbm_batch_destroy": [_P],
+    "cslbm2d_workspace_bytes": [ctypes.POINTER(Params2D), ctypes.POINTER(_SZ)],
+    "cslbm2d_create": [ctypes.POINTER(Params2D), _P, _SZ, _P, ctypes.POINTER(_P)],
+    "cslbm2d_destroy": [_P],
+    "cslbm2d_set_metric": [_P, _P, _P, _I],
+    "cslbm2d_set_jacobian": [_P, _P, _I],
+    "cslbm2d_update_metric": [_P, _P, _P, _P, _I],
+    "cslbm2d_set_boundary_velocity": [_P, _I, _I, _P, _I],
+    "cslbm2d_init_equilibrium": [_P, _P, _P, _I],
+    "cslbm2d_step": [_P, _I],
+    "cslbm2d_get_moments": [_P, _P, _P, _I, _I],
+    "cslbm2d_total_mass": [_P, _D],
+    "cslbm2d_wall_force": [_P, _I, _I, _D],
     "cslbm_last_error": [],
 }
 

@@ -336,3 +336,103 @@ class CurvedBatch:
             self.close()
         except Exception:
             pass
+
+
+class CurvedLattice2D:
+    """A D2Q9 lattice n = (n0, n1) carrying a metric field (the library's
+    cslbm2d_* calls, one method each).  bc per axis as for CurvedLattice;
+    storage "fp32" or "fp64"."""
+
+    def __init__(self, n, bc_lo=(0, 0), bc_hi=None, tau=0.8, theta=0.0, fext=(0.0, 0.0), storage="fp32",
+                 device=None, stream=None):
+        torch = _torch()
+        _abi.load()
+        self.n = tuple(int(v) for v in n)
+        self.N = int(np.prod(self.n))
+        bc_hi = bc_lo if bc_hi is None else bc_hi
+        self.params = _abi.Params2D((ctypes.c_int * 2)(*self.n), (ctypes.c_int * 2)(*bc_lo),
+                                    (ctypes.c_int * 2)(*bc_hi), float(tau), float(theta),
+                                    (ctypes.c_double * 2)(*fext), STORAGE[storage])
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        nb = ctypes.c_size_t(0)
+        call("cslbm2d_workspace_bytes", ctypes.byref(self.params), ctypes.byref(nb))
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self.ctx = ctypes.c_void_p()
+        call("cslbm2d_create", ctypes.byref(self.params), self.workspace.data_ptr(), nb.value,
+             self.stream.cuda_stream, ctypes.byref(self.ctx))
+
+    def _arg(self, a, rows):
+        if a is None:
+            return None, 1, None
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            t = a.to(self.device, torch.float64).contiguous()
+            return t.data_ptr(), 1, t
+        h = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        return h.ctypes.data, 0, h
+
+    def set_metric(self, g3, dg6):
+        p1, d1, k1 = self._arg(g3, 3)
+        p2, d2, k2 = self._arg(dg6, 6)
+        if d1 != d2:
+            raise ValueError("g3 and dg6 must both be host or both device arrays")
+        call("cslbm2d_set_metric", self.ctx, p1, p2, d1)
+
+    def set_jacobian(self, J4):
+        p, d, k = self._arg(J4, 4)
+        call("cslbm2d_set_jacobian", self.ctx, p, d)
+
+    def set_chart(self, chart):
+        self.set_metric(chart.g3, chart.dg6)
+        self.set_jacobian(chart.J4)
+
+    def update_metric(self, g3, dg6, J4):
+        p1, d1, k1 = self._arg(g3, 3)
+        p2, d2, k2 = self._arg(dg6, 6)
+        p3, d3, k3 = self._arg(J4, 4)
+        if not (d1 == d2 == d3):
+            raise ValueError("metric inputs must all be host or all device arrays")
+        call("cslbm2d_update_metric", self.ctx, p1, p2, p3, d1)
+
+    def set_boundary_velocity(self, axis, side, u2):
+        p, d, k = self._arg(u2, 2)
+        call("cslbm2d_set_boundary_velocity", self.ctx, int(axis), int(side), p, d)
+        self._keep_face = getattr(self, "_keep_face", {})
+        self._keep_face[(axis, side)] = k
+
+    def init_equilibrium(self, rho=None, u=None):
+        p1, d1, k1 = self._arg(rho, 1)
+        p2, d2, k2 = self._arg(u, 2)
+        on_dev = d1 if rho is not None else d2
+        call("cslbm2d_init_equilibrium", self.ctx, p1, p2, on_dev)
+
+    def step(self, nsteps=1):
+        call("cslbm2d_step", self.ctx, int(nsteps))
+
+    def moments(self, cartesian=False):
+        rho = np.empty(self.N)
+        u = np.empty((2, self.N))
+        call("cslbm2d_get_moments", self.ctx, rho.ctypes.data, u.ctypes.data, int(cartesian), 0)
+        return rho, u
+
+    def total_mass(self):
+        out = ctypes.c_double(0.0)
+        call("cslbm2d_total_mass", self.ctx, ctypes.byref(out))
+        return out.value
+
+    def wall_force(self, axis, side):
+        out = (ctypes.c_double * 2)()
+        call("cslbm2d_wall_force", self.ctx, int(axis), int(side), out)
+        return np.array(out[:])
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            _abi.load().cslbm2d_destroy(self.ctx)
+        self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
