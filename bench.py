@@ -345,6 +345,63 @@ def bench_side(args):
     print(json.dumps(line), flush=True)
 
 
+# algorithmic bytes per D2Q9 node update (FP32): 9 slots read + written, 6
+# forcing coefficients read + written, 10 geometry values read
+BYTES_PER_NODE_2D = 9 * 4 * 2 + 6 * 4 * 2 + 10 * 4
+
+
+def bench_d2q9(args):
+    """The D2Q9 path on a 4096 x 1024 periodic channel (walls across, the top
+    wall displaced by 6 % of the height x cos(2 pi x / 4096), body-force
+    drive, FP32): MLUPS and the fraction of the measured HBM bandwidth against
+    160 B per node update; 10 LBM steps per bench step."""
+    import torch
+
+    from paper_1803_07822_gb300.lattice import CurvedLattice2D
+    torch.cuda.set_device(0)
+    n = (4096, 1024)
+    H = n[1] - 1
+    x = I.grid2d(n)[0]
+    k = 2 * np.pi / n[0]
+    a = 0.06 * H
+    ch = I.channel_chart2d(n, a * np.cos(k * x), -a * k * np.sin(k * x), -a * k * k * np.cos(k * x))
+    tau = 0.8
+    F = 8.0 * (tau - 0.5) / 3.0 * 0.05 / H ** 2
+    lat = CurvedLattice2D(n, (0, 1), (0, 1), tau=tau, fext=(F, 0.0), storage="fp32")
+    lat.set_chart(ch)
+    lat.init_equilibrium()
+    N = lat.N
+    for _ in range(args.warmup):
+        lat.step(STEPS_PER_CYCLE)
+    clocks = Clocks(0)
+    clocks.wait_first()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        lat.step(STEPS_PER_CYCLE)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    step_ms = ms / (args.steps * STEPS_PER_CYCLE)
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_NODE_2D * N / (step_ms * 1e-3) / 1e9
+    line = {"metric": "curved-space LBM MLUPS (D2Q9)", "value": N * STEPS_PER_CYCLE * args.steps / (ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "D2Q9 periodic deformed channel 4096x1024, 6 % cosine top wall, body force, FP32",
+                       "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
+                       "l2": "inputs > L2 (0.7 GB of state per LBM step), no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind, "kernel": "one LBM step: k2_momentum + k2_step",
+                         "bytes_per_node": BYTES_PER_NODE_2D, "step_ms": step_ms},
+            "gpu_launches": 2 * STEPS_PER_CYCLE * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def adjoint_report(step_kernel, steps=None):
     """Adjoint/forward step-time ratio on the adjoint-form channel
     (inputs.adjoint_channel: 64 x 128 x 64, 32 deformation coefficients,
@@ -520,7 +577,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
     ap.add_argument("--workload", default="dynamic",
-                    choices=["dynamic", "target256", "crop64", "batch64", "adjoint64", "lgrad"])
+                    choices=["dynamic", "target256", "crop64", "batch64", "adjoint64", "lgrad", "d2q9"])
     ap.add_argument("--adjoint-steps", type=int, default=ADJOINT_STEPS,
                     help="LBM steps of the adjoint objective (adjoint64 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -539,6 +596,8 @@ def main():
         return bench_batch(args)
     if args.workload in ("adjoint64", "lgrad"):
         return bench_side(args)
+    if args.workload == "d2q9":
+        return bench_d2q9(args)
 
     import torch
 

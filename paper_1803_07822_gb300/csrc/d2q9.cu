@@ -10,13 +10,14 @@
 // non-periodic face normal, wall > inflow > outflow), the node-wise chart
 // change (Sec. IV.B).
 //
-// State (pull slots): slot (l, v) holds the post-collision value of node v
-// for direction l less the weight w_l (small numbers near rest, which FP32
-// keeps to more digits); a node gathers f_l = slot(l, v - c_l) + w_l +
-// F_l(v)/2, F(v) recomposed from the node's stored forcing coefficients (A,
-// B, C of its last step), which are also the history F(t - dt) of the next
-// collision.  So one step is two kernels: rho u of every node (the gradient
-// stencil needs it), then the step of every node into the other buffers.
+// State (pull slots, h-form): slot (l, v) holds the post-collision value of
+// node v for direction l less the weight w_l, so that a node pulls
+// h_l = slot(l, v - c_l) = f_l - w_l - F_l(t - dt)/2 (small numbers near
+// rest, which FP32 keeps to more digits); the node's stored forcing
+// coefficients A, B, C are the history F(t - dt), whose moments enter rho,
+// j and Pi in closed form.  So one step is two kernels: rho u of every node
+// (the gradient stencil needs it), then the step of every node into the
+// other buffers.
 // One thread per node; R = float (FP32 storage and arithmetic) or double.
 #include <cstdint>
 #include <cstring>
@@ -44,8 +45,7 @@ __host__ __device__ __forceinline__ constexpr double wq(int l)
     return l == 0 ? 4.0 / 9.0 : (l <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-// geometry per node: sqrt(g), g^00, g^01, g^11, Gamma^0_{00,01,11}, Gamma^1_{00,01,11}
-constexpr int NG = 10;
+// geometry per node (10 values): sqrt(g), g^00, g^01, g^11, Gamma^0_{00,01,11}, Gamma^1_{00,01,11}
 // forcing coefficients per node: A, B^0, B^1, C^00, C^01, C^11
 constexpr int NF = 6;
 
@@ -125,23 +125,33 @@ template <class R> __device__ __forceinline__ void load_fc(const R* __restrict__
     for (int k = 0; k < NF; k++) out[k] = Fc[k * N + v];
 }
 
-// the streamed populations of an interior node, less their weights:
-// s_l = slot (l, x - c_l) + F_l(x) / 2 = f_l - w_l
+// h of an interior node: the pulled slots, h_l = slot (l, x - c_l) =
+// f_l - w_l - F_l(t - dt)/2 (periodic wrap at most)
 template <class R>
-__device__ __forceinline__ void gather(const Lat& L, const R* __restrict__ P, const R* __restrict__ Fc,
-                                       const R* __restrict__ G, int x, int y, R f[Q])
+__device__ __forceinline__ void gather_h(const Lat& L, const R* __restrict__ P, int x, int y, R h[Q])
 {
-    const long long N = L.N, v = x + (long long)L.n[0] * y;
-    R fc[NF];
-    load_fc(Fc, N, v, fc);
-    const R isg = R(1) / G[v];
+    const long long N = L.N;
 #pragma unroll
     for (int l = 0; l < Q; l++) {
         int xs = x - cx(l), ys = y - cy(l);
         wrap(L, 0, xs);
         wrap(L, 1, ys);
-        f[l] = P[l * N + xs + (long long)L.n[0] * ys] + R(0.5) * forcing_l<R>(l, isg, fc);
+        h[l] = P[l * N + xs + (long long)L.n[0] * ys];
     }
+}
+
+// s = f - w of an interior node: h + F(t - dt)/2 of the node
+template <class R>
+__device__ __forceinline__ void gather(const Lat& L, const R* __restrict__ P, const R* __restrict__ Fc,
+                                       const R* __restrict__ G, int x, int y, R f[Q])
+{
+    const long long v = x + (long long)L.n[0] * y;
+    R fc[NF];
+    load_fc(Fc, L.N, v, fc);
+    const R isg = R(1) / G[v];
+    gather_h<R>(L, P, x, y, f);
+#pragma unroll
+    for (int l = 0; l < Q; l++) f[l] += R(0.5) * forcing_l<R>(l, isg, fc);
 }
 
 // moments of f from s = f - w: rho = sqrt(g)(1 + sum s), j = sqrt(g) sum s c,
@@ -165,6 +175,21 @@ template <class R> __device__ __forceinline__ void moments(const R f[Q], R sg, R
     Pi[0] = sg * (m2[0] + R(1.0 / 3.0));
     Pi[1] = sg * m2[1];
     Pi[2] = sg * (m2[2] + R(1.0 / 3.0));
+}
+
+// moments of f from h = f - w - F(t - dt)/2 and that history (A, B, C):
+// rho = sqrt(g)(1 + sum h) + A/2, j = sqrt(g) sum h c + B/2,
+// Pi = sqrt(g)(sum h c c + delta/3) + C/2 (sum F sqrt(g) = A, sum F c sqrt(g) = B, sum F c c sqrt(g) = C)
+template <class R>
+__device__ __forceinline__ void moments_h(const R h[Q], R sg, const R Fo[NF], R& rho, R j[2], R Pi[3])
+{
+    moments<R>(h, sg, rho, j, Pi);
+    rho += R(0.5) * Fo[0];
+    j[0] += R(0.5) * Fo[1];
+    j[1] += R(0.5) * Fo[2];
+    Pi[0] += R(0.5) * Fo[3];
+    Pi[1] += R(0.5) * Fo[4];
+    Pi[2] += R(0.5) * Fo[5];
 }
 
 // rule of a node on a non-periodic face (0: none), its inner node and face
@@ -228,20 +253,24 @@ __device__ __noinline__ void face_pops(const Lat& L, const R* __restrict__ P, co
     for (int l = 0; l < Q; l++) f[l] = few[l] + (fi[l] - fei[l]) * ratio;
 }
 
-// the populations a node sees: gathered, or the boundary rule on a face node
+// what a node sees, in h-form: the pulled slots, or on a face node the
+// boundary rule's s less F(t - dt)/2 of the node; Fo the node's history
 template <class R>
-__device__ __forceinline__ void node_pops(const Lat& L, const R* __restrict__ P, const R* __restrict__ Fc,
-                                          const R* __restrict__ G, int x, int y, R f[Q])
+__device__ __forceinline__ void node_state(const Lat& L, const R* __restrict__ P, const R* __restrict__ Fc,
+                                           const R* __restrict__ G, int x, int y, R h[Q], R Fo[NF])
 {
+    const long long v = x + (long long)L.n[0] * y;
+    load_fc(Fc, L.N, v, Fo);
     int axis = 0, side = 0, ix, iy;
     const int bc = classify(L, x, y, axis, side, ix, iy);
     if (bc == 0) {
-        gather<R>(L, P, Fc, G, x, y, f);
+        gather_h<R>(L, P, x, y, h);
     } else {
         R ff[Q];
         face_pops<R>(L, P, Fc, G, x, y, bc, axis, side, ix, iy, ff);
+        const R isg = R(1) / G[v];
 #pragma unroll
-        for (int l = 0; l < Q; l++) f[l] = ff[l];
+        for (int l = 0; l < Q; l++) h[l] = ff[l] - R(0.5) * forcing_l<R>(l, isg, Fo);
     }
 }
 
@@ -290,21 +319,19 @@ __global__ void __launch_bounds__(TB) k2_momentum(Lat L, const R* __restrict__ P
     const long long v = blockIdx.x * (long long)TB + threadIdx.x;
     if (v >= L.N) return;
     const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R f[Q], rho, j[2], Pi[3];
-    node_pops<R>(L, P, Fc, G, x, y, f);
-    moments<R>(f, G[v], rho, j, Pi);
+    R h[Q], Fo[NF], rho, j[2], Pi[3];
+    node_state<R>(L, P, Fc, G, x, y, h, Fo);
+    moments_h<R>(h, G[v], Fo, rho, j, Pi);
     jf[v] = j[0];
     jf[L.N + v] = j[1];
 }
 
-// the forcing coefficients of a node from its populations f, geometry and the rho u field
+// the forcing coefficients of a node from its moments (rho, j, Pi), geometry
+// and the rho u field; fe returns f^eq - w
 template <class R>
 __device__ __forceinline__ void forcing_coeffs(const Lat& L, const R* __restrict__ jf, int x, int y, const Geo<R>& g,
-                                               const R f[Q], R& rho, R j[2], R out[NF])
+                                               R rho, const R j[2], const R Pi[3], R fe[Q], R out[NF])
 {
-    R Pi[3];
-    moments<R>(f, g.sg, rho, j, Pi);
-    R fe[Q];
     feq_all<R>(g, R(L.theta), rho, j, fe);
     // T = Pi^eq + (1 - 1/2tau) (Pi - Pi^eq)
     R Peq[3] = {R(0), R(0), R(0)};
@@ -323,12 +350,24 @@ __device__ __forceinline__ void forcing_coeffs(const Lat& L, const R* __restrict
     T[0][0] = Peq[0] + kv * (Pi[0] - Peq[0]);
     T[0][1] = T[1][0] = Peq[1] + kv * (Pi[1] - Peq[1]);
     T[1][1] = Peq[2] + kv * (Pi[2] - Peq[2]);
-    // D[k][i] = 3 sum_l w_l c_l^k (rho u^i)(x + c_l)
+    // D[k][i] = 3 sum_l w_l c_l^k (rho u^i)(x + c_l); an interior node's
+    // stencil needs no ghost (periodic wrap at most)
     R D[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
+    const bool inner = (x > 0 || L.lo[0] == PER) && (x < L.n[0] - 1 || L.hi[0] == PER) &&
+                       (y > 0 || L.lo[1] == PER) && (y < L.n[1] - 1 || L.hi[1] == PER);
 #pragma unroll
     for (int l = 1; l < Q; l++) {
         R jn[2];
-        jsite<R>(L, jf, x + cx(l), y + cy(l), jn);
+        if (inner) {
+            int xs = x + cx(l), ys = y + cy(l);
+            wrap(L, 0, xs);
+            wrap(L, 1, ys);
+            const long long u = xs + (long long)L.n[0] * ys;
+            jn[0] = jf[u];
+            jn[1] = jf[L.N + u];
+        } else {
+            jsite<R>(L, jf, x + cx(l), y + cy(l), jn);
+        }
         const R w = R(3.0 * wq(l));
 #pragma unroll
         for (int i = 0; i < 2; i++) {
@@ -388,7 +427,7 @@ __device__ __forceinline__ void forcing_coeffs(const Lat& L, const R* __restrict
 // collision f* = f - (f - f^eq)/tau + F(t) - F(t - dt)/2 into the node's own
 // slots, the new coefficients into the node's history
 template <class R>
-__global__ void __launch_bounds__(TB) k2_step(Lat L, const R* __restrict__ P, R* __restrict__ Pout,
+__global__ void __launch_bounds__(TB, 4) k2_step(Lat L, const R* __restrict__ P, R* __restrict__ Pout,
                                               const R* __restrict__ Fc, R* __restrict__ Fout,
                                               const R* __restrict__ G, const R* __restrict__ jf)
 {
@@ -396,19 +435,21 @@ __global__ void __launch_bounds__(TB) k2_step(Lat L, const R* __restrict__ P, R*
     if (v >= L.N) return;
     const long long N = L.N;
     const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R f[Q];
-    node_pops<R>(L, P, Fc, G, x, y, f);
+    R h[Q], Fo[NF];
+    node_state<R>(L, P, Fc, G, x, y, h, Fo);
     Geo<R> g;
     load_geo(G, N, v, g);
-    R rho, j[2], Fn[NF], Fo[NF];
-    forcing_coeffs<R>(L, jf, x, y, g, f, rho, j, Fn);
-    load_fc(Fc, N, v, Fo);
-    R fe[Q];
-    feq_all<R>(g, R(L.theta), rho, j, fe);
+    R rho, j[2], Pi[3], Fn[NF], fe[Q];
+    moments_h<R>(h, g.sg, Fo, rho, j, Pi);
+    forcing_coeffs<R>(L, jf, x, y, g, rho, j, Pi, fe, Fn);
+    // f* - w = (1 - omega) h + omega (f^eq - w) + F(t) - omega F(t - dt)/2, with
+    // s = h + F(t - dt)/2: one recomposition of the combined coefficients
     const R om = R(L.omega);
+    R K[NF];
 #pragma unroll
-    for (int l = 0; l < Q; l++)
-        Pout[l * N + v] = f[l] - om * (f[l] - fe[l]) + forcing_l<R>(l, g.isg, Fn) - R(0.5) * forcing_l<R>(l, g.isg, Fo);
+    for (int k = 0; k < NF; k++) K[k] = Fn[k] - R(0.5) * om * Fo[k];
+#pragma unroll
+    for (int l = 0; l < Q; l++) Pout[l * N + v] = (R(1) - om) * h[l] + om * fe[l] + forcing_l<R>(l, g.isg, K);
 #pragma unroll
     for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
 }
@@ -447,12 +488,13 @@ __global__ void __launch_bounds__(TB) k2_init_force(Lat L, const R* __restrict__
     const long long v = blockIdx.x * (long long)TB + threadIdx.x;
     if (v >= L.N) return;
     const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R f[Q];
-    node_pops<R>(L, P, Fc0, G, x, y, f);
+    R h[Q], Fo[NF];
+    node_state<R>(L, P, Fc0, G, x, y, h, Fo);
     Geo<R> g;
     load_geo(G, L.N, v, g);
-    R rho, j[2], Fn[NF];
-    forcing_coeffs<R>(L, jf, x, y, g, f, rho, j, Fn);
+    R rho, j[2], Pi[3], fe[Q], Fn[NF];
+    moments_h<R>(h, g.sg, Fo, rho, j, Pi);
+    forcing_coeffs<R>(L, jf, x, y, g, rho, j, Pi, fe, Fn);
 #pragma unroll
     for (int k = 0; k < NF; k++) Fc[k * L.N + v] = Fn[k];
 }
@@ -529,10 +571,9 @@ __global__ void __launch_bounds__(TB) k2_transform(Lat L, const R* __restrict__ 
     if (v >= L.N) return;
     const long long N = L.N;
     const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R f[Q], rho, j[2], Pi[3], fc[NF];
-    node_pops<R>(L, P, Fc, Gold, x, y, f);
-    moments<R>(f, Gold[v], rho, j, Pi);
-    load_fc(Fc, N, v, fc);
+    R h[Q], rho, j[2], Pi[3], fc[NF];
+    node_state<R>(L, P, Fc, Gold, x, y, h, fc);
+    moments_h<R>(h, Gold[v], fc, rho, j, Pi);
     const double a = Jn4[v], b = Jn4[N + v], c = Jn4[2 * N + v], d = Jn4[3 * N + v], id = 1.0 / (a * d - b * c);
     const double ni[2][2] = {{d * id, -b * id}, {-c * id, a * id}};
     const double o[2][2] = {{Jo4[v], Jo4[N + v]}, {Jo4[2 * N + v], Jo4[3 * N + v]}};
@@ -595,9 +636,9 @@ __global__ void __launch_bounds__(TB) k2_readout(Lat L, const R* __restrict__ P,
     if (v >= L.N) return;
     const long long N = L.N;
     const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R f[Q], rho, j[2], Pi[3];
-    node_pops<R>(L, P, Fc, G, x, y, f);
-    moments<R>(f, G[v], rho, j, Pi);
+    R h[Q], Fo[NF], rho, j[2], Pi[3];
+    node_state<R>(L, P, Fc, G, x, y, h, Fo);
+    moments_h<R>(h, G[v], Fo, rho, j, Pi);
     const double u0 = double(j[0]) / double(rho), u1 = double(j[1]) / double(rho);
     rho_out[v] = double(rho);
     if (cartesian) {
@@ -639,9 +680,9 @@ __global__ void __launch_bounds__(TB) k2_mass(Lat L, const R* __restrict__ P, co
     double val[1] = {0.0};
     if (v < L.N) {
         const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-        R f[Q], rho, j[2], Pi[3];
-        node_pops<R>(L, P, Fc, G, x, y, f);
-        moments<R>(f, G[v], rho, j, Pi);
+        R h[Q], Fo[NF], rho, j[2], Pi[3];
+        node_state<R>(L, P, Fc, G, x, y, h, Fo);
+        moments_h<R>(h, G[v], Fo, rho, j, Pi);
         val[0] = double(G[v]) * double(rho);
     }
     block_add<1>(val, acc);
@@ -661,11 +702,11 @@ __global__ void __launch_bounds__(TB) k2_wall_force(Lat L, const R* __restrict__
         r[axis] = side ? L.n[axis] - 1 : 0;
         r[other] = (int)t;
         const long long N = L.N, v = r[0] + (long long)L.n[0] * r[1];
-        R f[Q], rho, j[2], Pi[3], fe[Q];
-        node_pops<R>(L, P, Fc, G, r[0], r[1], f);
+        R h[Q], Fo[NF], rho, j[2], Pi[3], fe[Q];
+        node_state<R>(L, P, Fc, G, r[0], r[1], h, Fo);
         Geo<R> g;
         load_geo(G, N, v, g);
-        moments<R>(f, g.sg, rho, j, Pi);
+        moments_h<R>(h, g.sg, Fo, rho, j, Pi);
         feq_all<R>(g, R(L.theta), rho, j, fe);
         R Peq[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -867,12 +908,10 @@ cslbm_status cslbm2d_create(const cslbm2d_params* p, void* ws, size_t bytes, voi
     c->G[1] = b + off[5];
     c->jf = b + off[6];
     c->J = (double*)(b + off[7]);
-    double* faces = (double*)(b + off[8]);
     for (int a = 0; a < 2; a++)
         for (int s = 0; s < 2; s++) c->face[a * 2 + s] = nullptr;
     c->stage = (double*)(b + off[9]);
     c->scratch = (double*)(b + off[10]);
-    (void)faces;
     if (cudaMemsetAsync(ws, 0, need, c->stream) != cudaSuccess) {
         delete c;
         return fail2(CSLBM_ECUDA, "memset failed");

@@ -85,7 +85,8 @@ def test_reparametrised_poiseuille(storage):
     n = (4, 17)
     ch = I.reparam_chart2d(n, 0.1)
     w = dict(n=n, chart=ch, bc_lo=(0, 1), bc_hi=(0, 1), tau=1.0)
-    g, o = pair(w, storage, fext=(2e-5, 0.0))
+    # drive for U_max = 0.05: F = 8 nu U / L^2
+    g, o = pair(w, storage, fext=(8.0 * (1.0 - 0.5) / 3.0 * 0.05 / 16 ** 2, 0.0))
     g.step(1500)
     o.step(1500)
     rg, ug = g.moments(cartesian=True)
