@@ -603,6 +603,16 @@ __device__ __forceinline__ void block_reduce_add(double (&val)[K], double* acc)
     }
 }
 
+// rho of a face node (the boundary rule), out of line: few nodes take it
+template <class S, class R>
+__device__ __noinline__ R face_rho(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                   const R* __restrict__ geo, int x, int y, int z, long long v, R sg)
+{
+    NodeMoments<S, R> M;
+    node_moments<S, R>(L, P, hist, geo, x, y, z, v, sg, M);
+    return M.rho;
+}
+
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_mass(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
                                               const R* __restrict__ geo, double* acc)
@@ -613,9 +623,17 @@ __global__ void __launch_bounds__(TPB) k_mass(Lat L, const S* __restrict__ P, co
         int x, y, z;
         node_coords(L, v, x, y, z);
         const R sg = geo[v];
-        NodeMoments<S, R> M;
-        node_moments<S, R>(L, P, hist, geo, x, y, z, v, sg, M);
-        val[0] = double(sg) * double(M.rho);
+        R rho;
+        if (on_boundary(L, x, y, z)) {
+            rho = face_rho<S, R>(L, P, hist, geo, x, y, z, v, sg);
+        } else {
+            // rho = sqrt(g)(1 + sum s) + A/2 of the pulled populations (the same sums as node_moments)
+            R s[Q], m0, m1[3], m2[6];
+            gather_raw<S, R>(L, P, x, y, z, s);
+            sums(s, m0, m1, m2);
+            rho = sg * (R(1) + m0) + R(0.5) * hist[v];
+        }
+        val[0] = double(sg) * double(rho);
     }
     block_reduce_add<1>(val, acc);
 }
