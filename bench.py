@@ -163,23 +163,29 @@ class Clocks:
 
 
 def dist_setup(args):
+    """(rank, world, local) from the launcher's environment; a process group
+    when world > 1 -- NCCL on the GPUs, gloo where there is no GPU (the
+    host-logic tests).  Every rank then runs its own, independent problem."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     import torch
-    torch.cuda.set_device(local)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, world, local
 
 
 def reduce_max(x, world):
+    """The maximum of x over the ranks (the job's time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -188,6 +194,12 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def whole_job_mlups(world, nodes_per_rank, lbm_steps, ms):
+    """Whole-job throughput: every rank updates its own nodes_per_rank nodes
+    lbm_steps times; ms is the slowest rank's time (weak scaling)."""
+    return world * nodes_per_rank * lbm_steps / (ms * 1e-3) / 1e6
 
 
 def oracle_cycle_sample(spec, steps, warm):
@@ -664,7 +676,7 @@ def main():
     ms = reduce_max(ms, world)
     ok = lat.check()
     ms_per_step = ms / args.steps
-    value = world * N * STEPS_PER_CYCLE * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, N, STEPS_PER_CYCLE * args.steps, ms)
 
     peak, peak_kind = peaks()
     step_ms = step_ms_total / max(nprof, 1)
