@@ -231,8 +231,9 @@ void rows_prepare(cslbm_ctx* c)
     bool ok = true;
     for (int k = 0; k < 2 && ok; k++) {
         const cuuint64_t pd[4] = {n0, n1, n2, 19}, ps[3] = {n0 * sb, n0 * n1 * sb, N * sb};
-        const cuuint32_t pb[4] = {(cuuint32_t)n0, TR, 1, 1};
+        const cuuint32_t pb[4] = {(cuuint32_t)n0, TR, 1, 1}, pb3[4] = {(cuuint32_t)n0, TR, 1, 3};
         ok = ok && mk(&R.pop[k], tpop, 4, c->P[k], pd, ps, pb);
+        ok = ok && mk(&R.pop3[k], tpop, 4, c->P[k], pd, ps, pb3);
         const cuuint64_t gd[2] = {N, 25}, gs[1] = {N * 4};
         const cuuint32_t gb[2] = {NT, 25};
         ok = ok && mk(&R.geo[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->G[k], gd, gs, gb);

@@ -96,7 +96,7 @@ __device__ __forceinline__ void momentum_node(const Lat& L, const S* __restrict_
     R s[Q];
 #pragma unroll
     for (int l = 0; l < Q; l++)
-        s[l] = R(Store<S>::ld(P + (unsigned)l * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
+        s[l] = R(Store<S>::ld(P + (unsigned)pslot(l) * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
     PairSums<R> Ps;
     pair_sums(s, Ps);
     R m1[3];
@@ -192,7 +192,7 @@ __device__ __forceinline__ void step_core(const Lat& L, const R s[Q], const GeoT
 #pragma unroll
     for (int a = 0; a < 6; a++) hout[(4 + a) * N + v] = H.C[a];
 #pragma unroll
-    for (int l = 0; l < Q; l++) Store<S>::st(Pout + (unsigned)l * N + v, out[l]);
+    for (int l = 0; l < Q; l++) Store<S>::st(Pout + (unsigned)pslot(l) * N + v, out[l]);
 }
 
 template <class R>
@@ -265,7 +265,7 @@ __device__ __forceinline__ void step_node(const Lat& L, const S* __restrict__ Pi
     R s[Q];
 #pragma unroll
     for (int l = 0; l < Q; l++)
-        s[l] = R(Store<S>::ld(Pin + (unsigned)l * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
+        s[l] = R(Store<S>::ld(Pin + (unsigned)pslot(l) * N + nbr_off(src, cvec(l, 0), cvec(l, 1), cvec(l, 2))));
     GeoT<R> G;
     HistT<R> Hp;
     load_geo_hist(geo, hin, v, N, G, Hp);

@@ -39,7 +39,7 @@ namespace cslbm {
 namespace rows {
 
 struct FMaps {
-    CUtensorMap pop, jf, geo, hist, geo1, hist4;
+    CUtensorMap pop, pop3, jf, geo, hist, geo1, hist4;  // pop3: boxes of three population planes
 };
 
 // first moment and density of an interior node i with pulled populations s,
@@ -106,8 +106,9 @@ static __device__ __noinline__ bool face_momentum(const Lat& L, int xi, int yi, 
     return global;
 }
 
-// copies of the momentum stage of tile t: the 19 population boxes (or rows
-// at a periodic y seam), sqrt(g), and A, B of the history
+// copies of the momentum stage of tile t: the population boxes (9 grouped
+// boxes when a tile is NT nodes, else 19; rows at a periodic y seam),
+// sqrt(g), and A, B of the history
 template <class S>
 __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FMaps& M, int t, unsigned char* st,
                                           unsigned long long* bar, const S* __restrict__ Pin, int lane,
@@ -120,23 +121,33 @@ __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FM
     const bool yper = L.bclo[1] == BC_PERIODIC, zper = L.bclo[2] == BC_PERIODIC;
     const unsigned v0 = ((unsigned)z * n1 + y0) * n0;
     const bool seam = yper && (y0 == 0 || y0 + pl.TR >= n1);
-    const int npop = seam ? Q * TRe : Q;
+    const bool grouped = !seam && pl.TR * n0 == NT;
+    const int npop = seam ? Q * TRe : (grouped ? PGROUPS : Q);
     for (int c = lane; c < npop + 2; c += 32) {
+        if (c < npop && grouped) {
+            const int base = pgroup_base(c), cnt = pgroup_count(c), d = pgroup_dir(c);
+            bool in = true;
+            const int zs = wrap_or(z - cvec_rt(d, 2), n2, zper, in);
+            bar_expect_tx(bar, (unsigned)(cnt * pl.TR * n0 * sizeof(S)));
+            tensor4(st + (size_t)base * NT * sizeof(S), cnt == 3 ? &M.pop3 : &M.pop, 0, y0 - cvec_rt(d, 1), zs, base,
+                    bar);
+            continue;
+        }
         if (c < npop) {
-            const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0;
+            const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0, q = pslot_rt(l);
             bool in = true;
             const int zs = wrap_or(z - cvec_rt(l, 2), n2, zper, in);
             if (!seam) {
                 const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
                 bar_expect_tx(bar, bytes);
-                tensor4(st + (size_t)l * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, l, bar);
+                tensor4(st + (size_t)q * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, q, bar);
                 continue;
             }
             const int ys = wrap_or(y0 + r - cvec_rt(l, 1), n1, yper, in);
             if (!in) continue;
             const unsigned bytes = (unsigned)(n0 * sizeof(S));
             bar_expect_tx(bar, bytes);
-            bulk_copy(st + (size_t)(l * NT + r * n0) * sizeof(S), Pin + (size_t)l * N + ((unsigned)zs * n1 + ys) * n0,
+            bulk_copy(st + (size_t)(q * NT + r * n0) * sizeof(S), Pin + (size_t)q * N + ((unsigned)zs * n1 + ys) * n0,
                       bytes, bar);
         } else if (c == npop) {
             bar_expect_tx(bar, NT * 4u);
@@ -174,7 +185,7 @@ __device__ __forceinline__ void mom_tile(const Lat& L, const Plan& pl, const uns
 #pragma unroll
         for (int l = 0; l < Q; l++) {
             const int cx = cvec(l, 0);
-            sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
+            sv[l] = to_f(pop[pslot(l) * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
         }
         sg = gs[q0];
         A = hs[q0];
@@ -332,7 +343,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 asm volatile("fence.proxy.async.global;\n" ::: "memory");
             }
             dep = __shfl_sync(0xffffffffu, dep, 0);
-            issue_tile<S>(L, pl, &M.pop, &M.jf, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
+            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
                           dep ? (PART_MAIN | PART_JF) : PART_MAIN);
             if (lane == 0 && ks + 1 < K) pre = ld_acquire(done + dep_iteration(L, pl, t + G, G));
             __syncwarp();
@@ -432,6 +443,7 @@ int launch_fused_step(cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* e
     const float* geo = (const float*)c->G[gc];
     rows::FMaps M;
     M.pop = R.pop[pc];
+    M.pop3 = R.pop3[pc];
     M.jf = R.jf;
     M.geo = R.geo[gc];
     M.hist = R.hist[hc];

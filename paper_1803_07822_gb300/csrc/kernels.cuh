@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TPB) k_init_scatter(Lat L, const double* __res
                 else ok = false;
             }
         }
-        if (ok) Store<S>::st(P + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), hermite_l(l, G.isg, b0, j, a2, tr));
+        if (ok) Store<S>::st(P + (long long)pslot(l) * L.N + nidx(L, r[0], r[1], r[2]), hermite_l(l, G.isg, b0, j, a2, tr));
     }
 }
 
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(TPB) k_half_shift(Lat L, S* __restrict__ P, co
             }
         }
         if (ok) {
-            S* p = P + (long long)l * L.N + nidx(L, r[0], r[1], r[2]);
+            S* p = P + (long long)pslot(l) * L.N + nidx(L, r[0], r[1], r[2]);
             Store<S>::st(p, Store<S>::ld(p) - R(0.5) * forcing_l(l, isg, H));
         }
     }
@@ -364,7 +364,7 @@ __device__ __forceinline__ void transform_store(const Lat& L, S* __restrict__ Po
         if (!ok) continue;
         // f~ - F~/2 - w  with  f~ - w = w/sqrt(g~) [(rho - sqrt g~) + ...]
         R val = hermite_l(l, isgn, rho - sgn, j2, P2, trP2) - R(0.5) * forcing_l(l, isgn, Hn);
-        Store<S>::st(Pout + (long long)l * L.N + nidx(L, r[0], r[1], r[2]), val);
+        Store<S>::st(Pout + (long long)pslot(l) * L.N + nidx(L, r[0], r[1], r[2]), val);
     }
 }
 

@@ -35,6 +35,27 @@ __host__ __device__ __forceinline__ constexpr int cvec(int l, int a)
                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1},  {0, -1, 1}};
     return t[l][a];
 }
+// Storage plane of direction l in a population buffer [19][N]: the
+// directions that share (c_y, c_z) -- and so pull from the same row -- lie
+// next to each other, 0 1 2 | 3 7 10 | 4 8 9 | 5 11 14 | 6 12 13 | 15 | 16 |
+// 17 | 18, so that one copy of three planes stages the rows they pull.
+__host__ __device__ __forceinline__ constexpr int pslot(int l)
+{
+    constexpr int t[Q] = {0, 1, 2, 3, 6, 9, 12, 4, 7, 8, 5, 10, 13, 14, 11, 15, 16, 17, 18};
+    return t[l];
+}
+// the same for a runtime l, from two words of 5-bit fields (no table in local memory)
+__device__ __forceinline__ int pslot_rt(int l)
+{
+    const unsigned long long a = 0x515072312618820ull, b = 0x4a307adcdull;
+    return (int)((l < 12 ? a >> (5 * l) : b >> (5 * (l - 12))) & 31ull);
+}
+// the nine staging groups: first plane, number of planes, and a direction of the group
+__host__ __device__ __forceinline__ constexpr int pgroup_base(int g) { return g < 5 ? 3 * g : g + 10; }
+__host__ __device__ __forceinline__ constexpr int pgroup_count(int g) { return g < 5 ? 3 : 1; }
+__host__ __device__ __forceinline__ constexpr int pgroup_dir(int g) { return g == 0 ? 0 : (g < 5 ? g + 2 : g + 10); }
+constexpr int PGROUPS = 9;
+
 // Weights of the lattice quadrature: 1/3 rest, 1/18 faces, 1/36 edges.
 __host__ __device__ __forceinline__ constexpr double wq(int l)
 {
@@ -188,7 +209,7 @@ __device__ __forceinline__ void gather_raw(const Lat& L, const S* __restrict__ P
         int xs = wrapc(x - cvec(l, 0), L.n[0]);
         int ys = wrapc(y - cvec(l, 1), L.n[1]);
         int zs = wrapc(z - cvec(l, 2), L.n[2]);
-        s[l] = R(Store<S>::ld(P + (long long)l * L.N + nidx(L, xs, ys, zs)));
+        s[l] = R(Store<S>::ld(P + (long long)pslot(l) * L.N + nidx(L, xs, ys, zs)));
     }
 }
 

@@ -133,19 +133,23 @@ __device__ __forceinline__ int wrap_or(int r, int n, bool periodic, bool& inside
 // Tensor maps handed to the pass (grid constants: a copy instruction must
 // name a map in parameter, constant or global memory, never a local copy).
 struct Maps {
-    CUtensorMap pop, jf, geo, hist;
+    CUtensorMap pop, pop3, jf, geo, hist;  // pop3: boxes of three population planes
 };
 
 // the copy warp: stage the rows of tile t into stage `st`, completing on bar.
-// Tiles away from the ends of a periodic y axis take one box per population,
-// per rho u layer, and for the geometry and the history (24 copies); the
+// Tiles away from the ends of a periodic y axis take one box per group of
+// populations that pull from the same row (three planes, or one: 9 boxes)
+// when a tile is NT nodes, else one box per population, then one per rho u
+// layer, and one each for the geometry and the history (14 copies); the
 // first and last tile of a periodic y axis copy row by row, so that the rows
-// across the periodic seam come from the other end of the axis.
+// across the periodic seam come from the other end of the axis.  The number
+// of copies, not their bytes, is what the copy engine pays for.
 constexpr int PART_MAIN = 1, PART_JF = 2;  // populations + geometry + history / rho u
 
 template <class S>
 __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const CUtensorMap* mpop,
-                                           const CUtensorMap* mjf, const CUtensorMap* mgeo, const CUtensorMap* mhist,
+                                           const CUtensorMap* mpop3, const CUtensorMap* mjf,
+                                           const CUtensorMap* mgeo, const CUtensorMap* mhist,
                                            int t, unsigned char* st,
                                            unsigned long long* bar, const S* __restrict__ Pin,
                                            const Mom4<float>* __restrict__ jf, int lane, int part, int stride = 32)
@@ -157,19 +161,29 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
     const bool yper = L.bclo[1] == BC_PERIODIC, zper = L.bclo[2] == BC_PERIODIC;
     const unsigned v0 = ((unsigned)z * n1 + y0) * n0;
     const bool seam = yper && (y0 == 0 || y0 + pl.TR >= n1);
-    const int npop = seam ? Q * TRe : Q, njf = seam ? 3 * (TRe + 2) : 3;
+    const bool grouped = !seam && pl.TR * n0 == NT;
+    const int npop = seam ? Q * TRe : (grouped ? PGROUPS : Q), njf = seam ? 3 * (TRe + 2) : 3;
     const int total = npop + njf + 2;
     for (int c = lane; c < total; c += stride) {
         const bool is_jf = c >= npop && c < npop + njf;
         if (!(part & (is_jf ? PART_JF : PART_MAIN))) continue;
+        if (c < npop && grouped) {
+            // planes base .. base + cnt - 1 pull from the same row (y0 - c_y, z - c_z)
+            const int base = pgroup_base(c), cnt = pgroup_count(c), d = pgroup_dir(c);
+            bool in = true;
+            const int zs = wrap_or(z - cvec_rt(d, 2), n2, zper, in);
+            bar_expect_tx(bar, (unsigned)(cnt * pl.TR * n0 * sizeof(S)));
+            tensor4(st + (size_t)base * NT * sizeof(S), cnt == 3 ? mpop3 : mpop, 0, y0 - cvec_rt(d, 1), zs, base, bar);
+            continue;
+        }
         if (c < npop) {
-            const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0;
+            const int l = seam ? c / TRe : c, r = seam ? c - l * TRe : 0, q = pslot_rt(l);
             bool in = true;
             const int zs = wrap_or(z - cvec_rt(l, 2), n2, zper, in);
             if (!seam) {
                 const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
                 bar_expect_tx(bar, bytes);
-                tensor4(st + (size_t)l * NT * sizeof(S), mpop, 0, y0 - cvec_rt(l, 1), zs, l, bar);
+                tensor4(st + (size_t)q * NT * sizeof(S), mpop, 0, y0 - cvec_rt(l, 1), zs, q, bar);
                 continue;
             }
             const int y = y0 + r;
@@ -177,7 +191,7 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
             if (!in) continue;
             const unsigned bytes = (unsigned)(n0 * sizeof(S));
             bar_expect_tx(bar, bytes);
-            bulk_copy(st + (size_t)(l * NT + r * n0) * sizeof(S), Pin + (size_t)l * N + ((unsigned)zs * n1 + ys) * n0,
+            bulk_copy(st + (size_t)(q * NT + r * n0) * sizeof(S), Pin + (size_t)q * N + ((unsigned)zs * n1 + ys) * n0,
                       bytes, bar);
         } else if (c < npop + njf) {
             const int k = c - npop, a = seam ? k / (TRe + 2) : k, b = seam ? k - a * (TRe + 2) : 0;
@@ -243,7 +257,7 @@ __device__ __forceinline__ void step_tile(const Lat& L, const Plan& pl, const un
 #pragma unroll
         for (int l = 0; l < Q; l++) {
             const int cx = cvec(l, 0);
-            sv[l] = to_f(pop[l * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
+            sv[l] = to_f(pop[pslot(l) * NT + (cx == 0 ? q0 : (cx > 0 ? qm : qp))]);
         }
         G.sg = gs[q0];
 #pragma unroll
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                 if (!__all_sync(0xffffffffu, ok)) break;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            issue_tile<S>(L, pl, &M.pop, &M.jf, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s],
+            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s],
                           Pin, jf, lane, PART_MAIN | PART_JF);
             __syncwarp();
             if (lane == 0) bar_arrive(&full[s]);
@@ -363,6 +377,7 @@ int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, i
     if (pl.ntiles > 0) {
         rows::Maps M;
         M.pop = R.pop[pc];
+        M.pop3 = R.pop3[pc];
         M.jf = R.jf;
         M.geo = R.geo[gc];
         M.hist = R.hist[hc];
