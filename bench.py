@@ -49,7 +49,8 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
 # of its passes touch every node once, so the bytes scale with the nodes);
 # the fused pass (k_step_fused + k_step_faces) on the 128x128x256 channel
 # itself.  FP32 storage; only valid for the kernels as they were captured.
-MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
+MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288,
+                                ("fused", "fp32"): (1194091105.5 + 505491760.8 + 32555741.1 + 3770.2) / 4194304}
 
 
 def step_pass(n, storage, step_kernel, axis2_periodic=False):
