@@ -49,8 +49,11 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
 # of its passes touch every node once, so the bytes scale with the nodes);
 # the fused pass (k_step_fused + k_step_faces) on the 128x128x256 channel
 # itself.  FP32 storage; only valid for the kernels as they were captured.
-MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288,
-                                ("fused", "fp32"): (1194091105.5 + 505491760.8 + 32555741.1 + 3770.2) / 4194304}
+MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
+# the fused pass changed (one box for the three rho u layers) after its last
+# launch list (413 B per node with the face kernel): no current figure
+TRAFFIC_NOTE = {"fused": "no capture of the current kernel; 413 B/node (fused + faces) measured before the "
+                         "three rho u layers became one copy (profiles/launches_dynamic_channel_128x128x256.md)"}
 
 
 def step_pass(n, storage, step_kernel, axis2_periodic=False):
@@ -696,6 +699,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "one LBM step: " + PASS_KERNELS[sp], "bytes_per_node": bpn,
+                     "traffic_note": TRAFFIC_NOTE.get(sp),
                      "step_ms": step_ms},
         "e2e": e2e,
         "gpu_launches": launches,

@@ -251,6 +251,10 @@ void rows_prepare(cslbm_ctx* c)
     const cuuint64_t jd[2] = {JL, 4 * N / JL}, js[1] = {JL * 4};
     const cuuint32_t jb[2] = {(cuuint32_t)JL, (cuuint32_t)R.plan.JR};
     ok = ok && mk(&R.jf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->jf, jd, js, jb);
+    // the same lines per plane, three planes per box
+    const cuuint64_t jd3[3] = {JL, 4 * n0 * n1 / JL, n2}, js3[2] = {JL * 4, n0 * n1 * 16};
+    const cuuint32_t jb3[3] = {(cuuint32_t)JL, (cuuint32_t)R.plan.JR, 3};
+    ok = ok && mk(&R.jf3, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->jf, jd3, js3, jb3);
     if (!ok) return;
     R.ok = 1;
     // the fused form: momentum and step in one cooperative launch

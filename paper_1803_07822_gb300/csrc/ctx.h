@@ -23,6 +23,7 @@ struct cslbm_rows {
     CUtensorMap pop[2];   // [19][n2][n1][n0] populations, box n0 x TR
     CUtensorMap pop3[2];  // the same, box n0 x TR x 1 x 3 (three planes that pull from one row)
     CUtensorMap jf;       // rho u as [4 N / JL][JL] floats, box JL x JR (the TR + 2 rows of a layer)
+    CUtensorMap jf3;      // rho u as [n2][4 n0 n1 / JL][JL] floats, box JL x JR x 3 (three layers)
     CUtensorMap geo[2];   // [25][N] geometry, box NT x 25
     CUtensorMap hist[2];  // [10][N] history, box NT x 10
     CUtensorMap geo1[2];  // sqrt(g) alone, box NT x 1

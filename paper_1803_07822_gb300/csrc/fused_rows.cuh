@@ -39,7 +39,7 @@ namespace cslbm {
 namespace rows {
 
 struct FMaps {
-    CUtensorMap pop, pop3, jf, geo, hist, geo1, hist4;  // pop3: boxes of three population planes
+    CUtensorMap pop, pop3, jf, jf3, geo, hist, geo1, hist4;  // pop3: three population planes; jf3: three rho u layers
 };
 
 // first moment and density of an interior node i with pulled populations s,
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 asm volatile("fence.proxy.async.global;\n" ::: "memory");
             }
             dep = __shfl_sync(0xffffffffu, dep, 0);
-            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
+            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.jf3, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
                           dep ? (PART_MAIN | PART_JF) : PART_MAIN);
             if (lane == 0 && ks + 1 < K) pre = ld_acquire(done + dep_iteration(L, pl, t + G, G));
             __syncwarp();
@@ -444,6 +444,7 @@ int launch_fused_step(cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* e
     rows::FMaps M;
     M.pop = R.pop[pc];
     M.pop3 = R.pop3[pc];
+    M.jf3 = R.jf3;
     M.jf = R.jf;
     M.geo = R.geo[gc];
     M.hist = R.hist[hc];

@@ -109,6 +109,15 @@ __device__ __forceinline__ void tensor2(void* dst, const CUtensorMap* map, int c
         "l"(map), "r"(c0), "r"(c1), "r"(su32(b))
         : "memory");
 }
+__device__ __forceinline__ void tensor3(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                        unsigned long long* b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(su32(b))
+        : "memory");
+}
 __device__ __forceinline__ void tensor4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                         unsigned long long* b)
 {
@@ -133,7 +142,7 @@ __device__ __forceinline__ int wrap_or(int r, int n, bool periodic, bool& inside
 // Tensor maps handed to the pass (grid constants: a copy instruction must
 // name a map in parameter, constant or global memory, never a local copy).
 struct Maps {
-    CUtensorMap pop, pop3, jf, geo, hist;  // pop3: boxes of three population planes
+    CUtensorMap pop, pop3, jf, jf3, geo, hist;  // pop3: three population planes; jf3: three rho u layers
 };
 
 // the copy warp: stage the rows of tile t into stage `st`, completing on bar.
@@ -149,7 +158,8 @@ constexpr int PART_MAIN = 1, PART_JF = 2;  // populations + geometry + history /
 template <class S>
 __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const CUtensorMap* mpop,
                                            const CUtensorMap* mpop3, const CUtensorMap* mjf,
-                                           const CUtensorMap* mgeo, const CUtensorMap* mhist,
+                                           const CUtensorMap* mjf3, const CUtensorMap* mgeo,
+                                           const CUtensorMap* mhist,
                                            int t, unsigned char* st,
                                            unsigned long long* bar, const S* __restrict__ Pin,
                                            const Mom4<float>* __restrict__ jf, int lane, int part, int stride = 32)
@@ -162,7 +172,10 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
     const unsigned v0 = ((unsigned)z * n1 + y0) * n0;
     const bool seam = yper && (y0 == 0 || y0 + pl.TR >= n1);
     const bool grouped = !seam && pl.TR * n0 == NT;
-    const int npop = seam ? Q * TRe : (grouped ? PGROUPS : Q), njf = seam ? 3 * (TRe + 2) : 3;
+    // the three rho u layers z - 1 .. z + 1 in one box when they are planes of
+    // the lattice and the stage holds them without padding
+    const bool jf_one = !seam && pl.JS == (pl.TR + 2) * n0 && z >= 1 && z + 1 <= n2 - 1;
+    const int npop = seam ? Q * TRe : (grouped ? PGROUPS : Q), njf = seam ? 3 * (TRe + 2) : (jf_one ? 1 : 3);
     const int total = npop + njf + 2;
     for (int c = lane; c < total; c += stride) {
         const bool is_jf = c >= npop && c < npop + njf;
@@ -193,6 +206,11 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
             bar_expect_tx(bar, bytes);
             bulk_copy(st + (size_t)(q * NT + r * n0) * sizeof(S), Pin + (size_t)q * N + ((unsigned)zs * n1 + ys) * n0,
                       bytes, bar);
+        } else if (c < npop + njf && jf_one) {
+            // rows y0 - 1 .. y0 + TR of planes z - 1 .. z + 1 (row -1 of the first
+            // tile is the fill: only face rows use it)
+            bar_expect_tx(bar, (unsigned)(3 * (pl.TR + 2) * n0 * sizeof(Mom4<float>)));
+            tensor3(st + pl.off_jf, mjf3, 0, (y0 - 1) * 4 * n0 / pl.JL, z - 1, bar);
         } else if (c < npop + njf) {
             const int k = c - npop, a = seam ? k / (TRe + 2) : k, b = seam ? k - a * (TRe + 2) : 0;
             bool in = true;
@@ -326,7 +344,8 @@ __global__ void __launch_bounds__(NTHR, 1)
                 if (!__all_sync(0xffffffffu, ok)) break;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes, &full[s],
+            issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.jf3, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes,
+                          &full[s],
                           Pin, jf, lane, PART_MAIN | PART_JF);
             __syncwarp();
             if (lane == 0) bar_arrive(&full[s]);
@@ -378,6 +397,7 @@ int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, i
         rows::Maps M;
         M.pop = R.pop[pc];
         M.pop3 = R.pop3[pc];
+        M.jf3 = R.jf3;
         M.jf = R.jf;
         M.geo = R.geo[gc];
         M.hist = R.hist[hc];
