@@ -44,16 +44,16 @@ STEPS_PER_CYCLE = 10
 BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 + 80 + 100,
                   "bf16": 19 * 2 * 2 + 80 + 100, "fp64": 19 * 8 * 2 + 80 + 100}
 # DRAM bytes per node update (dram__bytes_read.sum + dram__bytes_write.sum of
-# the kernels of one LBM step, per launch, divided by the nodes) from ncu
-# launch lists: the flat pass on the 64x128x64 crop of the same channel (both
-# of its passes touch every node once, so the bytes scale with the nodes);
-# the fused pass (k_step_fused + k_step_faces) on the 128x128x256 channel
-# itself.  FP32 storage; only valid for the kernels as they were captured.
-MEASURED_DRAM_BYTES_PER_NODE = {("flat", "fp32"): (120.483328e6 + 39.361792e6 + 47.349504e6 + 0.097536e6) / 524288}
-# the fused pass changed (one box for the three rho u layers) after its last
-# launch list (413 B per node with the face kernel): no current figure
+# the kernels of one LBM step, per launch, divided by the nodes) from an ncu
+# launch list of the kernels as they stand, keyed by (pass, storage).  Empty:
+# both step passes changed after their last captures, so the line reports
+# traffic null with the older figure in a note.
+MEASURED_DRAM_BYTES_PER_NODE = {}
 TRAFFIC_NOTE = {"fused": "no capture of the current kernel; 413 B/node (fused + faces) measured before the "
-                         "three rho u layers became one copy (profiles/launches_dynamic_channel_128x128x256.md)"}
+                         "three rho u layers became one copy (profiles/launches_dynamic_channel_128x128x256.md)",
+                "flat": "no capture of the current kernel; 395 B/node (both flat passes, 64x128x64 crop) measured "
+                        "before the population planes were reordered into staging groups "
+                        "(profiles/k_step_flat_crop_64x128x64.md)"}
 
 
 def step_pass(n, storage, step_kernel, axis2_periodic=False):
