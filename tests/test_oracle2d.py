@@ -3,8 +3,10 @@ the flat metric reduces it to textbook D2Q9 BGK; rest stays at rest and mass
 is conserved; plane Poiseuille flow between walls on the nodes; the same flow
 under a re-parametrised (curved) metric converges to the analytic Cartesian
 profile; the wall force at rest is pressure times length; a chart change to
-the same chart leaves the moments."""
+the same chart leaves the moments; the boundary nodes carry the fields their
+rules define."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_1803_07822_gb300 import inputs as I
@@ -117,3 +119,54 @@ def test_transform_to_the_same_chart_keeps_the_moments():
     o.transform(ch.g3, ch.dg6, ch.J4, ch.J4)
     r1, u1 = o.moments(ch.J4)
     assert np.abs(r1 - r0).max() < 1e-14 and np.abs(u1 - u0).max() < 1e-14
+
+
+def _boundary_rule2(n, bc_lo, bc_hi, r):
+    prio = {1: 3, 2: 2, 3: 1}
+    best, inner = None, list(r)
+    for a in range(2):
+        for s, bc in ((0, bc_lo[a]), (1, bc_hi[a])):
+            if bc == P or r[a] != (0 if s == 0 else n[a] - 1):
+                continue
+            inner[a] = r[a] + (1 if s == 0 else -1)
+            if best is None or prio[bc] > prio[best[0]]:
+                best = (bc, a, s)
+    return None if best is None else (*best, tuple(inner))
+
+
+@pytest.mark.parametrize("bcs", [((2, 1), (3, 1)), ((2, 2), (3, 3)), ((3, 2), (1, 3))])
+def test_boundary_fields_on_every_boundary_node(bcs):
+    """What the boundary rules mean, on a curved state after a few steps: a
+    wall or inflow node carries the inner node's density and the imposed
+    contravariant velocity, an outflow node the inner node's density and
+    velocity; the inner node is one step inward along every non-periodic face
+    of the node, and the rule is the one of highest priority (wall > inflow >
+    outflow, then the lower axis, then the low side)."""
+    bc_lo, bc_hi = bcs
+    w = I.flag_channel((11, 9), amp=0.05, tau=0.8)
+    n = w["n"]
+    rng = np.random.default_rng(5)
+    faces = {}
+    o = oracle.Lattice2D(n, bc_lo, bc_hi, tau=0.8)
+    o.set_metric(w["chart"].g3, w["chart"].dg6)
+    for a in range(2):
+        for s, bc in ((0, bc_lo[a]), (1, bc_hi[a])):
+            if bc in (1, 2):
+                faces[(a, s)] = 0.01 * rng.standard_normal((2, n[1 - a]))
+                o.set_face_velocity(a, s, faces[(a, s)])
+    o.init()
+    o.step(10)
+    rho, u = o.moments()
+    seen = set()
+    for y in range(n[1]):
+        for x in range(n[0]):
+            rule = _boundary_rule2(n, bc_lo, bc_hi, (x, y))
+            if rule is None:
+                continue
+            bc, a, s, inner = rule
+            v, vi = x + n[0] * y, inner[0] + n[0] * inner[1]
+            seen.add(bc)
+            assert abs(rho[v] - rho[vi]) < 1e-13 * rho[vi]
+            want = u[:, vi] if bc == 3 else faces[(a, s)][:, (x, y)[1 - a]]
+            assert np.abs(u[:, v] - want).max() < 1e-14, ((x, y), bc)
+    assert seen == {bc for bc in bc_lo + bc_hi if bc}
