@@ -8,8 +8,7 @@ expansion, App. B; lattice gradient, App. D; transformation, Sec. IV.B).
 
 Parity unpinned (no printed value to match; held only by convergence and
 invariant tests): the sqrt(g) factor on the non-equilibrium part of the wall
-rule, the ghost extrapolation of rho u at faces and the transformation
-variants.
+rule and the transformation variants.
 """
 from __future__ import annotations
 
