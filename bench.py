@@ -23,6 +23,8 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -239,6 +241,52 @@ def oracle_cycle_sample(spec, steps, warm):
     N = int(np.prod(n))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return N * STEPS_PER_CYCLE * steps / t_total / 1e6, t_total, n, cores
+
+
+ORACLE_C1_STEPS = 200
+
+
+def oracle_c1_sample():
+    """The FP64 oracle on the 16 x 16 x 32 plain channel (walls, body force,
+    one-mode deformation), ORACLE_C1_STEPS timed steps after 20, with the
+    threads OpenMP was given in this process.  Returns (MLUPS, seconds)."""
+    import oracle
+    w = I.plain_fp64_channel()
+    o = oracle.Lattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+    o.set_metric(w["chart"].g6, w["chart"].dg18)
+    o.init()
+    o.step(20)
+    t0 = time.perf_counter()
+    o.step(ORACLE_C1_STEPS)
+    dt = time.perf_counter() - t0
+    return int(np.prod(w["n"])) * ORACLE_C1_STEPS / dt / 1e6, dt
+
+
+def oracle_single_thread():
+    """oracle_c1_sample in a child process started with OMP_NUM_THREADS=1."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-c1"], capture_output=True, text=True,
+                       timeout=600, env=dict(os.environ, OMP_NUM_THREADS="1"), cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("single-thread oracle run failed:\n" + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": 1,
+            "sample": f"16x16x32 plain FP64 channel, {ORACLE_C1_STEPS} steps after 20 ({d['secs']:.1f} s)"}
+
+
+def cpu_model(path="/proc/cpuinfo"):
+    """The host CPU as /proc/cpuinfo names it: the model name where there is
+    one (x86), else the implementer and part codes (Arm)."""
+    try:
+        with open(path) as fh:
+            txt = fh.read()
+    except OSError:
+        return platform.machine()
+    m = re.search(r"^model name\s*:\s*(.+)$", txt, re.M)
+    if m:
+        return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", txt, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", txt, re.M)
+    return f"{platform.machine()}, implementer {imp.group(1) if imp else '?'}, part {part.group(1) if part else '?'}"
 
 
 def bench_batch(args):
@@ -602,7 +650,12 @@ def main():
     ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16", "fp64"],
                     help="storage of the populations (default: the workload's, FP32)")
+    ap.add_argument("--oracle-c1", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_c1:  # the child process of oracle_single_thread
+        v, secs = oracle_c1_sample()
+        print(json.dumps({"value": v, "secs": secs}), flush=True)
+        return None
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -714,7 +767,8 @@ def main():
         mlups, secs, n, cores = oracle_cycle_sample(spec, 2, 0)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, 2 cycles "
-                                          f"(transform + {STEPS_PER_CYCLE} steps + reductions), FP64"}
+                                          f"(transform + {STEPS_PER_CYCLE} steps + reductions), FP64",
+                                "cpu": cpu_model(), "single_thread": oracle_single_thread()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

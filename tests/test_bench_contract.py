@@ -1,7 +1,9 @@
-"""The benchmark's reference arm on CPU: `bench.py --impl reference` times the
-FP64 oracle on a bounded crop of the workload and prints one JSON line with
-the keys of the device arm plus impl, cpu_baseline and a zero-copy e2e; a
-rank other than 0 prints nothing and exits 0."""
+"""Host-side parts of the benchmark on CPU.  The reference arm
+(`bench.py --impl reference`) times the FP64 oracle on a bounded crop of the
+workload and prints one JSON line with the keys of the device arm plus impl,
+cpu_baseline and a zero-copy e2e; a rank other than 0 prints nothing and
+exits 0.  The device arm's cpu_baseline also carries a single-thread oracle
+timing (a child process with OMP_NUM_THREADS=1) and the host CPU's name."""
 import json
 import os
 import subprocess
@@ -37,3 +39,23 @@ def test_reference_arm_other_ranks_do_no_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_single_thread_oracle_timing_and_cpu_name(tmp_path):
+    b = _bench()
+    d = b.oracle_single_thread()
+    assert d["cores"] == 1 and d["value"] > 0 and d["unit"] == "MLUPS" and "16x16x32" in d["sample"]
+    arm = tmp_path / "cpuinfo"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    assert b.cpu_model(str(arm)).endswith("implementer 0x41, part 0xd4f")
+    x86 = tmp_path / "cpuinfo_x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\n")
+    assert b.cpu_model(str(x86)) == "Some CPU @ 2.0GHz"
