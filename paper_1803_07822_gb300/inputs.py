@@ -83,6 +83,28 @@ def reparam_position(n, eps):
     return x + eps * L / np.pi * np.sin(np.pi * x / L)
 
 
+def annulus_chart(n, r0):
+    """Polar chart of the gap between two concentric cylinders (lattice
+    units): axis 0 radial, r = r0 + x; axis 1 around the cylinders, theta =
+    y / r0 (unit arc at the inner cylinder, periodic for a flow that does not
+    depend on theta); axis 2 along them.  Flat space in curved coordinates,
+    g = diag(1, (r / r0)^2, 1)."""
+    x, y, _ = grid(n)
+    r, th = r0 + x, y / r0
+    c, s = np.cos(th), np.sin(th)
+    N = x.size
+    J9 = np.zeros((9, N))
+    J9[0], J9[1] = c, -(r / r0) * s
+    J9[3], J9[4] = s, (r / r0) * c
+    J9[8] = 1.0
+    hess = np.zeros((27, N))  # d_j d_k h^a at a*9 + j*3 + k
+    hess[0 * 9 + 0 * 3 + 1] = hess[0 * 9 + 1 * 3 + 0] = -s / r0
+    hess[0 * 9 + 1 * 3 + 1] = -(r / r0 ** 2) * c
+    hess[1 * 9 + 0 * 3 + 1] = hess[1 * 9 + 1 * 3 + 0] = c / r0
+    hess[1 * 9 + 1 * 3 + 1] = -(r / r0 ** 2) * s
+    return Chart(tuple(n), J9, hess)
+
+
 @dataclass
 class Deformation:
     """Wall displacement d(p, s) of the top wall and its derivatives, per node
