@@ -436,6 +436,21 @@ def reparam_chart2d(n, eps):
     return Chart2D(tuple(n), J4, hess)
 
 
+def annulus_chart2d(n, r0):
+    """annulus_chart in two dimensions: axis 0 radial (r = r0 + x), axis 1
+    around the cylinders (theta = y / r0); g = diag(1, (r / r0)^2)."""
+    x, y = grid2d(n)
+    r, th = r0 + x, y / r0
+    c, s = np.cos(th), np.sin(th)
+    J4 = np.stack([c, -(r / r0) * s, s, (r / r0) * c])
+    hess = np.zeros((8, x.size))  # d_j d_k h^a at a*4 + j*2 + k
+    hess[0 * 4 + 1] = hess[0 * 4 + 2] = -s / r0
+    hess[0 * 4 + 3] = -(r / r0 ** 2) * c
+    hess[1 * 4 + 1] = hess[1 * 4 + 2] = c / r0
+    hess[1 * 4 + 3] = -(r / r0 ** 2) * s
+    return Chart2D(tuple(n), J4, hess)
+
+
 def flag_channel(n=(257, 65), amp=0.05, width=0.15, center=0.35, re=100.0, tau=0.6):
     """2-D flag-like channel: walls at y = 0 and y = H, a parabolic inlet at x
     = 0 (centre-line speed from Re = U H / nu), an outlet at x = n0 - 1, the top

@@ -170,3 +170,37 @@ def test_boundary_fields_on_every_boundary_node(bcs):
             want = u[:, vi] if bc == 3 else faces[(a, s)][:, (x, y)[1 - a]]
             assert np.abs(u[:, v] - want).max() < 1e-14, ((x, y), bc)
     assert seen == {bc for bc in bc_lo + bc_hi if bc}
+
+
+def test_circular_couette_second_order():
+    """Circular Couette flow (Sec. V.B) on polar lattice coordinates: the
+    radius ratio 1.063 and Omega2 = -Omega1 of the paper, inner wall speed
+    1e-3; the Cartesian azimuthal profile converges at second order to
+    A r + B / r (B = (Omega1 - Omega2) R1^2 R2^2 / (R2^2 - R1^2))."""
+    errs = []
+    for m in (9, 17, 33):
+        L = m - 1
+        r0 = L / 0.063
+        n = (m, 4)
+        ch = I.annulus_chart2d(n, r0)
+        o = oracle.Lattice2D(n, (W, P), (W, P), tau=1.0)
+        o.set_metric(ch.g3, ch.dg6)
+        om1 = 1e-3 / r0
+        om2 = -om1
+        R1, R2 = r0, r0 + L
+        for side, om in ((0, om1), (1, om2)):
+            o.set_face_velocity(0, side, np.stack([np.zeros(4), np.full(4, om * r0)]))  # u^1 = v_theta r0 / r
+        o.init()
+        o.step(int(4 * L ** 2 * 6))
+        _, v = o.moments(ch.J4)
+        x, y = I.grid2d(n)
+        r, th = r0 + x, y / r0
+        vt = -np.sin(th) * v[0] + np.cos(th) * v[1]
+        A = (om2 * R2 ** 2 - om1 * R1 ** 2) / (R2 ** 2 - R1 ** 2)
+        B = (om1 - om2) * R1 ** 2 * R2 ** 2 / (R2 ** 2 - R1 ** 2)
+        ex = A * r + B / r
+        errs.append(np.linalg.norm(vt - ex) / np.linalg.norm(ex))
+        lin = om1 * R1 + (om2 * R2 - om1 * R1) * x / L
+        assert np.linalg.norm(lin - ex) / np.linalg.norm(ex) > 500 * errs[-1]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[0] < 2e-5 and np.all(rates > 1.9), (errs, rates)
