@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 from paper_1803_07822_gb300 import _abi
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -61,3 +63,32 @@ def test_2d_workspace_bytes_and_validation_without_gpu():
     q = _abi.Params2D((ctypes.c_int * 2)(257, 65), (ctypes.c_int * 2)(0, 1), (ctypes.c_int * 2)(3, 1), 0.6, 0.0,
                       (ctypes.c_double * 2)(0, 0), _abi.FP32)  # periodic on one side only
     assert lib.cslbm2d_workspace_bytes(ctypes.byref(q), ctypes.byref(n)) == _abi.EINVAL
+
+
+def _p3(n, lo, hi, tau=0.8, storage=None):
+    return _abi.Params((ctypes.c_int * 3)(*n), (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi), tau, 0.0,
+                       (ctypes.c_double * 3)(0, 0, 0), _abi.FP32 if storage is None else storage, 0)
+
+
+def test_degenerate_and_maximum_sizes_without_gpu():
+    """Sizes at the edges of what a context takes: an empty axis, a single
+    node (periodic), a non-periodic axis of 2 nodes, the 32-bit field offsets
+    (25 N < 2^32: the largest lattice is 171,798,691 nodes) and 65,535 planes."""
+    lib = _abi.load()
+    n = ctypes.c_size_t(0)
+    P, W = 0, 1
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((0, 4, 4), (P, P, P), (P, P, P))), ctypes.byref(n)) == _abi.EINVAL
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((1, 1, 1), (P, P, P), (P, P, P))), ctypes.byref(n)) == _abi.OK
+    assert n.value > 0
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((4, 4, 2), (P, P, W), (P, P, W))), ctypes.byref(n)) == _abi.EINVAL
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((4, 4, 3), (P, P, W), (P, P, W))), ctypes.byref(n)) == _abi.OK
+    # 555 x 555 x 557 = 171,569,925 nodes (89 GB of FP32 workspace) fits; one more plane does not
+    ok, big = (555, 555, 557), (555, 555, 558)
+    assert 25 * np.prod(ok, dtype=np.int64) < 2 ** 32 <= 25 * np.prod(big, dtype=np.int64)
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3(ok, (P, P, W), (P, P, W))), ctypes.byref(n)) == _abi.OK
+    per_node = n.value / np.prod(ok, dtype=np.int64)
+    assert 300 < per_node < 1000 and n.value < 280e9  # fits the GPU's memory with room to spare
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3(big, (P, P, W), (P, P, W))), ctypes.byref(n)) == _abi.EINVAL
+    assert b"too large" in lib.cslbm_last_error()
+    assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((4, 4, 65536), (P, P, P), (P, P, P))),
+                                     ctypes.byref(n)) == _abi.EINVAL
