@@ -83,7 +83,12 @@ typedef enum { CSLBM_STEP_AUTO = 0, CSLBM_STEP_FLAT = 1, CSLBM_STEP_ROWS = 2 } c
 
 typedef struct cslbm_ctx cslbm_ctx;
 
-/* Bytes of device workspace a context with these parameters needs. */
+/* Bytes of device workspace a context with these parameters needs (about
+ * 520 per node in FP32).  EINVAL for invalid parameters: an axis with no
+ * node, an axis periodic on one face only, a non-periodic axis of fewer than
+ * 3 nodes, tau <= 1/2, an unknown storage or step kernel, more than 65,535
+ * planes (n[2]), or 25 n0 n1 n2 >= 2^32 (the kernels' 32-bit field offsets:
+ * at most 171,798,691 nodes per context). */
 cslbm_status cslbm_workspace_bytes(const cslbm_params* p, size_t* bytes);
 
 /* Create a context on the current CUDA device.  `workspace` is caller-owned
