@@ -413,6 +413,35 @@ def bench_side(args):
 BYTES_PER_NODE_2D = 9 * 4 * 2 + 6 * 4 * 2 + 10 * 4
 
 
+def d2q9_channel(n):
+    """The D2Q9 benchmark channel at size n: periodic along x, walls across
+    y, the top wall displaced by 6 % of the height x cos(2 pi x / n0), body
+    force for a centre-line speed of 0.05 at tau 0.8.  (chart, tau, force)."""
+    H = n[1] - 1
+    x = I.grid2d(n)[0]
+    k = 2 * np.pi / n[0]
+    a = 0.06 * H
+    ch = I.channel_chart2d(n, a * np.cos(k * x), -a * k * np.sin(k * x), -a * k * k * np.cos(k * x))
+    tau = 0.8
+    return ch, tau, 8.0 * (tau - 0.5) / 3.0 * 0.05 / H ** 2
+
+
+def oracle2d_sample(n=(1024, 256), steps=40):
+    """The FP64 D2Q9 oracle on the same channel at a quarter of the size per
+    axis: `steps` timed steps after 2.  Returns (MLUPS, seconds, n, cores)."""
+    import oracle
+    ch, tau, F = d2q9_channel(n)
+    o = oracle.Lattice2D(n, (0, 1), (0, 1), tau=tau, fext=(F, 0.0))
+    o.set_metric(ch.g3, ch.dg6)
+    o.init()
+    o.step(2)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n[0] * n[1] * steps / dt / 1e6, dt, n, cores
+
+
 def bench_d2q9(args):
     """The D2Q9 path on a 4096 x 1024 periodic channel (walls across, the top
     wall displaced by 6 % of the height x cos(2 pi x / 4096), body-force
@@ -423,13 +452,7 @@ def bench_d2q9(args):
     from paper_1803_07822_gb300.lattice import CurvedLattice2D
     torch.cuda.set_device(0)
     n = (4096, 1024)
-    H = n[1] - 1
-    x = I.grid2d(n)[0]
-    k = 2 * np.pi / n[0]
-    a = 0.06 * H
-    ch = I.channel_chart2d(n, a * np.cos(k * x), -a * k * np.sin(k * x), -a * k * k * np.cos(k * x))
-    tau = 0.8
-    F = 8.0 * (tau - 0.5) / 3.0 * 0.05 / H ** 2
+    ch, tau, F = d2q9_channel(n)
     lat = CurvedLattice2D(n, (0, 1), (0, 1), tau=tau, fext=(F, 0.0), storage="fp32")
     lat.set_chart(ch)
     lat.init_equilibrium()
@@ -462,6 +485,11 @@ def bench_d2q9(args):
                          "traffic": None, "peak_kind": peak_kind, "kernel": "one LBM step: k2_momentum + k2_step",
                          "bytes_per_node": BYTES_PER_NODE_2D, "step_ms": step_ms},
             "gpu_launches": 2 * STEPS_PER_CYCLE * args.steps, "clocks": clk}
+    if not args.no_cpu_baseline:
+        v, secs, nc, cores = oracle2d_sample()
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"the same channel at {nc[0]}x{nc[1]}, 40 steps after 2, FP64 "
+                                          f"({secs:.1f} s)"}
     print(json.dumps(line), flush=True)
 
 

@@ -59,3 +59,11 @@ def test_single_thread_oracle_timing_and_cpu_name(tmp_path):
     x86 = tmp_path / "cpuinfo_x86"
     x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\n")
     assert b.cpu_model(str(x86)) == "Some CPU @ 2.0GHz"
+
+
+def test_d2q9_oracle_sample():
+    b = _bench()
+    v, secs, n, cores = b.oracle2d_sample(n=(64, 16), steps=3)
+    assert v > 0 and secs > 0 and n == (64, 16) and cores >= 1
+    ch, tau, F = b.d2q9_channel((4096, 1024))
+    assert tau == 0.8 and abs(F - 8.0 * 0.1 * 0.05 / 1023 ** 2) < 1e-18 and ch.J4.shape == (4, 4096 * 1024)
