@@ -644,6 +644,47 @@ def transform_interp_report(lat, dev, layout, reps=5):
                     "and reads 8 corners per node (20 fields + the FP64 Jacobian)"}
 
 
+def oracle_side_samples(spec):
+    """The FP64 oracle on a half-size crop of the bench channel (the same
+    generator at n / 2 per axis): the fourth-order lattice gradient of the six
+    metric components (App. D), and one chart change node-wise and with
+    interpolation (Sec. IV.B) between the snapshots t = 500 and 510.  Returns
+    the cpu_baseline objects of the lattice_gradient and transform_interp
+    reports."""
+    import oracle
+    n = tuple(v // 2 for v in spec["n"])
+    w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
+                          re=spec["re"])
+    (c0, f0), (c1, f1) = snapshots(w, [500.0, 510.0])
+    N = int(np.prod(n))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    crop = f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, FP64 oracle"
+    t0 = time.perf_counter()
+    oracle.lattice_gradient(n, c0.g6, 4, w["bc_lo"], w["bc_hi"])
+    dt_grad = time.perf_counter() - t0
+    wa = w["layout"][0]
+    psi = np.stack(I.grid(n))
+    psi[wa] = psi[wa] * c1.J9[wa * 3 + wa] / c0.J9[wa * 3 + wa]
+    times = {}
+    for mode in ("node", "interp"):
+        o = oracle.Lattice(n, w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+        o.set_metric(c0.g6, c0.dg18)
+        for (a, s), u in f0.items():
+            o.set_face_velocity(a, s, u)
+        o.init()
+        t0 = time.perf_counter()
+        if mode == "node":
+            o.transform(c1.g6, c1.dg18, c0.J9, c1.J9)
+        else:
+            o.transform_interp(c1.g6, c1.dg18, c0.J9, c1.J9, psi)
+        times[mode] = time.perf_counter() - t0
+    grad = {"value": N / dt_grad / 1e6, "unit": "Mnode/s", "cores": cores, "kind": "oracle",
+            "sample": f"order-4 gradient of the 6 metric components, {crop} ({dt_grad:.2f} s)"}
+    trans = {"node_wise_ms": times["node"] * 1e3, "interp_ms": times["interp"] * 1e3, "nodes": N, "cores": cores,
+             "kind": "oracle", "sample": f"one chart change (metric + transform) on the {crop}"}
+    return grad, trans
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -792,6 +833,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        grad_cpu, trans_cpu = oracle_side_samples(spec)
+        line["lattice_gradient"]["cpu_baseline"] = grad_cpu
+        line["transform_interp"]["cpu_baseline"] = trans_cpu
         mlups, secs, n, cores = oracle_cycle_sample(spec, 2, 0)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, 2 cycles "

@@ -67,3 +67,13 @@ def test_d2q9_oracle_sample():
     assert v > 0 and secs > 0 and n == (64, 16) and cores >= 1
     ch, tau, F = b.d2q9_channel((4096, 1024))
     assert tau == 0.8 and abs(F - 8.0 * 0.1 * 0.05 / 1023 ** 2) < 1e-18 and ch.J4.shape == (4, 4096 * 1024)
+
+
+def test_side_report_oracle_samples():
+    """The oracle timings that sit beside the lattice-gradient and
+    chart-change reports of the device line (run here on the profiling
+    workload's half-size crop)."""
+    b = _bench()
+    g, t = b.oracle_side_samples(b.workload_spec("crop64"))
+    assert g["kind"] == "oracle" and g["value"] > 0 and g["unit"] == "Mnode/s" and "32x64x32" in g["sample"]
+    assert t["kind"] == "oracle" and t["node_wise_ms"] > 0 and t["interp_ms"] > 0 and t["nodes"] == 32 * 64 * 32
