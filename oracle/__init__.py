@@ -8,7 +8,8 @@ expansion, App. B; lattice gradient, App. D; transformation, Sec. IV.B).
 
 Parity unpinned (no printed value to match; held only by convergence and
 invariant tests): the sqrt(g) factor on the non-equilibrium part of the wall
-rule and the transformation variants.
+rule, the Gamma rho u part of the covariant derivative inside the forcing
+moment C, and the transformation variants.
 """
 from __future__ import annotations
 

@@ -36,6 +36,11 @@
  * non-equilibrium extrapolation from the node one step inward along every
  * non-periodic face normal, linear ghost extrapolation for the gradient
  * stencil, wall force = s * sum J T^{in} sqrt(g).
+ *
+ * Parity unpinned (no printed value to match; held by convergence and
+ * invariant tests only): the sqrt(g) factor on the non-equilibrium part of the
+ * wall and inflow rule, the Gamma rho u part of the covariant derivative inside
+ * the forcing moment C, and the literal-a2 transformation variant.
  */
 #include <math.h>
 #include <stdlib.h>
