@@ -20,6 +20,11 @@
  *   (k * 3 + ij); sqrtg [N]; ginv4 [4][N] (full 2 x 2); gam8 [8][N] Gamma^i_jk
  *   at (i * 4 + j * 2 + k); J4 [4][N] J^a_i at (a * 2 + i); face velocity of
  *   face (axis, side): [2][n of the other axis], contravariant, NULL = 0.
+ *
+ * Parity unpinned, as in three dimensions: the sqrt(g) factor on the
+ * non-equilibrium part of the wall and inflow rule and the Gamma rho u part of
+ * the covariant derivative inside C (held by convergence and invariant tests
+ * only).
  */
 #include <math.h>
 #include <stdlib.h>
