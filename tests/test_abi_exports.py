@@ -5,6 +5,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 from paper_1803_07822_gb300 import _abi
 
@@ -92,3 +93,15 @@ def test_degenerate_and_maximum_sizes_without_gpu():
     assert b"too large" in lib.cslbm_last_error()
     assert lib.cslbm_workspace_bytes(ctypes.byref(_p3((4, 4, 65536), (P, P, P), (P, P, P))),
                                      ctypes.byref(n)) == _abi.EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises; there is no fallback."""
+    monkeypatch.setattr(_abi, "_lib", None)
+    monkeypatch.setattr(_abi._build, "LIB", str(tmp_path / "libcslbm.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _abi.load(build_if_missing=False)
+    monkeypatch.setattr(_abi._build, "nvcc", lambda: (_ for _ in ()).throw(RuntimeError("nvcc not found")))
+    monkeypatch.setattr(_abi._build, "up_to_date", lambda: False)
+    with pytest.raises(RuntimeError, match="nvcc"):
+        _abi.load()
