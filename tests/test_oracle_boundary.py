@@ -166,3 +166,28 @@ def test_reparametrised_couette_second_order():
         errs = np.array([run(m, eps=0.1)[0] for m in sizes])
         rates = np.log2(errs[:-1] / errs[1:])
         assert errs[0] < 2e-3 and np.all(rates > 1.8), (run.__name__, errs, rates)
+
+
+@pytest.mark.parametrize("nx,tau", [(9, 1.0), (17, 0.7), (12, 1.4)])
+def test_flat_couette_wall_force_is_the_exact_stress(nx, tau):
+    """Momentum transfer on the nodes (Sec. IV.A) in a flowing state: at
+    steady plane Couette flow the force of the fluid on each wall is the
+    exact viscous shear rho nu U / L (forward on the resting wall, backward
+    on the moving one) plus the pressure rho theta normal to the wall, per
+    wall node.  Exercises the non-equilibrium part of T (factor 1 - 1/2tau),
+    which the rest-state test cannot see."""
+    n = (nx, 1, 1)
+    L = nx - 1
+    nu = (tau - 0.5) / 3.0
+    ch = I.flat_chart(n)
+    lat = oracle.Lattice(n, (W, P, P), (W, P, P), tau=tau)
+    lat.set_metric(ch.g6, ch.dg18)
+    lat.set_face_velocity(0, 1, np.array([[0.0], [0.0], [U]]))
+    lat.init()
+    lat.step(int(6 * L ** 2 / nu))
+    rho, _ = lat.moments()
+    F0, F1 = lat.wall_force(0, 0, ch.J9), lat.wall_force(0, 1, ch.J9)
+    shear = rho.mean() * nu * U / L
+    assert abs(F0[2] - shear) < 1e-12 * shear and abs(F1[2] + shear) < 1e-12 * shear
+    assert abs(F0[0] + rho[0] / 3.0) < 1e-12 and abs(F1[0] - rho[-1] / 3.0) < 1e-12
+    assert abs(F0[1]) < 1e-15 and abs(F1[1]) < 1e-15
