@@ -204,3 +204,27 @@ def test_circular_couette_second_order():
         assert np.linalg.norm(lin - ex) / np.linalg.norm(ex) > 500 * errs[-1]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert errs[0] < 2e-5 and np.all(rates > 1.9), (errs, rates)
+
+
+def test_flat_couette_wall_force_is_the_exact_stress():
+    """Plane Couette flow between walls on the nodes y = 0 (at rest) and
+    y = L (moving at U along x): at steady state the force of the fluid on
+    each wall is the exact shear rho nu U / L per wall node (forward on the
+    resting wall, backward on the moving one) and the pressure rho theta
+    normal to it."""
+    for n1, tau in ((9, 1.0), (13, 0.7)):
+        n = (4, n1)
+        L = n1 - 1
+        nu = (tau - 0.5) / 3.0
+        U = 0.05
+        ch = I.flat_chart2d(n)
+        o = oracle.Lattice2D(n, (P, W), (P, W), tau=tau)
+        o.set_metric(ch.g3, ch.dg6)
+        o.set_face_velocity(1, 1, np.stack([np.full(4, U), np.zeros(4)]))
+        o.init()
+        o.step(int(6 * L ** 2 / nu))
+        rho, _ = o.moments()
+        F0, F1 = o.wall_force(1, 0, ch.J4), o.wall_force(1, 1, ch.J4)
+        shear = 4 * rho.mean() * nu * U / L
+        assert abs(F0[0] - shear) < 1e-12 * shear and abs(F1[0] + shear) < 1e-12 * shear, (F0, F1, shear)
+        assert abs(F0[1] + 4 * rho.mean() / 3) < 1e-11 and abs(F1[1] - 4 * rho.mean() / 3) < 1e-11
