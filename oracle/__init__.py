@@ -54,7 +54,7 @@ def _load():
                          "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
                          "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian",
                          "orc_transform_interp", "o2_lattice", "o2_geometry", "o2_init", "o2_step",
-                         "o2_moments", "o2_mass", "o2_wall_force", "o2_transform"):
+                         "o2_moments", "o2_mass", "o2_wall_force", "o2_transform", "o2_forcing_recompose"):
                 getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -300,6 +300,14 @@ def lattice2d():
     w = np.zeros(9)
     _load().o2_lattice(_p(c), _p(w))
     return c.reshape(9, 2), w
+
+
+def forcing_recompose2d(A, B2, C4, sqrtg):
+    """F_l [9] of one node from its forcing moments A, B [2], C [2x2] (Eq. forcing2 in 2-D)."""
+    out = np.zeros(9)
+    Bk, Ck = _f64(B2, (2,)), _f64(C4, (4,))
+    _load().o2_forcing_recompose(ctypes.c_double(A), _p(Bk), _p(Ck), ctypes.c_double(sqrtg), _p(out))
+    return out
 
 
 def geometry2d(n, g3, dg6):

@@ -316,6 +316,15 @@ static int check2(const o2_params *p)
     return p->tau > 0.5 ? 0 : -1;
 }
 
+/* single-node forcing recomposition F_l from A, B [2], C [4] (row-major), for
+ * the moment identities of the tests */
+int o2_forcing_recompose(double A, const double *B2, const double *C4, double sg, double *out9)
+{
+    const double B[2] = {B2[0], B2[1]}, C[2][2] = {{C4[0], C4[1]}, {C4[2], C4[3]}};
+    forcing2(A, B, C, sg, out9);
+    return 0;
+}
+
 int o2_init(const o2_params *p, const double *sqrtg, const double *ginv4, const double *gam8, const double *rho0,
             const double *u0, const double *const *uface, double *f, double *Fprev)
 {

@@ -228,3 +228,61 @@ def test_flat_couette_wall_force_is_the_exact_stress():
         shear = 4 * rho.mean() * nu * U / L
         assert abs(F0[0] - shear) < 1e-12 * shear and abs(F1[0] + shear) < 1e-12 * shear, (F0, F1, shear)
         assert abs(F0[1] + 4 * rho.mean() / 3) < 1e-11 and abs(F1[1] - 4 * rho.mean() / 3) < 1e-11
+
+
+def test_forcing_recomposition_moments_2d():
+    """The recomposed forcing carries the moments it is built from (Eq.
+    forcing2 in 2-D): sum F sqrt(g) = A, sum F c sqrt(g) = B, sum F c c
+    sqrt(g) = C, for random moments and sqrt(g) (the fourth moment of the
+    D2Q9 weights is isotropic)."""
+    c, w = oracle.lattice2d()
+    c = c.astype(float)
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        A = rng.standard_normal()
+        B = rng.standard_normal(2)
+        C = rng.standard_normal((2, 2))
+        C = C + C.T
+        sg = rng.uniform(0.7, 1.3)
+        F = oracle.forcing_recompose2d(A, B, C.ravel(), sg)
+        assert abs((F * sg).sum() - A) < 1e-13
+        assert np.abs(np.einsum("l,la->a", F * sg, c) - B).max() < 1e-13
+        assert np.abs(np.einsum("l,la,lb->ab", F * sg, c, c) - C).max() < 1e-13
+
+
+def test_mass_at_rest_is_the_area_of_the_chart():
+    """At rest (rho = 1) the mass sum sqrt(g) rho is the sum over the nodes of
+    |det J|, the area each node stands for in Cartesian space."""
+    w = I.flag_channel((40, 17), amp=0.08)
+    ch = w["chart"]
+    o = oracle.Lattice2D(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"])
+    o.set_metric(ch.g3, ch.dg6)
+    o.init()
+    detJ = np.abs(ch.J4[0] * ch.J4[3] - ch.J4[1] * ch.J4[2])
+    assert abs(o.mass() - detJ.sum()) < 1e-12 * detJ.sum()
+    assert abs(detJ.sum() - detJ.size) > 1e-3 * detJ.size  # the chart is not area-preserving
+
+
+def test_chart_change_keeps_density_and_cartesian_velocity():
+    """The node-wise chart change maps u to J~^-1 J u (Sec. IV.B), so every
+    fluid node keeps its density and its Cartesian velocity through a change
+    between two different charts."""
+    w0 = I.flag_channel((40, 17), amp=0.05)
+    w1 = I.flag_channel((40, 17), amp=0.09, center=0.5)
+    c0, c1 = w0["chart"], w1["chart"]
+    n = w0["n"]
+    rng = np.random.default_rng(8)
+    N = n[0] * n[1]
+    rho0 = 1.0 + 0.01 * rng.standard_normal(N)
+    u0 = 0.02 * rng.standard_normal((2, N))
+    o = oracle.Lattice2D(n, (P, W), (P, W), tau=0.8)
+    o.set_metric(c0.g3, c0.dg6)
+    o.init(rho0, u0)
+    r0, v0 = o.moments(c0.J4)
+    o.transform(c1.g3, c1.dg6, c0.J4, c1.J4)
+    r1, v1 = o.moments(c1.J4)
+    y = I.grid2d(n)[1]
+    fluid = (y > 0) & (y < n[1] - 1)
+    assert np.abs(r1 - r0)[fluid].max() < 1e-13
+    assert np.abs(v1 - v0)[:, fluid].max() < 1e-14
+    assert np.abs(c1.J4 - c0.J4).max() > 0.01  # the charts differ

@@ -53,6 +53,13 @@ CASES = [
      "for (int l = 0; l < Q2; l++) fout[l * N + v] = fin[l * N + vi] * sgi / sgw;",
      "for (int l = 0; l < Q2; l++) fout[l * N + v] = fin[l * N + vi];",
      "test_oracle2d.py::test_boundary_fields_on_every_boundary_node"),
+    ("2-D b2 without -c_s^2 delta A", SRC2,
+     "b2[a][b] = C[a][b] - CS2_2 * (a == b) * A;", "b2[a][b] = C[a][b];",
+     "test_oracle2d.py::test_forcing_recomposition_moments_2d"),
+    ("2-D transform with J J~^-1 for J~^-1 J", SRC2,
+     "D[i][j] = Jni[i][0] * Jo[0][j] + Jni[i][1] * Jo[1][j];",
+     "D[i][j] = Jo[i][0] * Jni[0][j] + Jo[i][1] * Jni[1][j];",
+     "test_oracle2d.py::test_chart_change_keeps_density_and_cartesian_velocity"),
 ]
 
 
