@@ -1,7 +1,8 @@
 """Pins of the oracle's interpolating chart change (Sec. IV.B, transition
 maps): it reduces to the node-wise transform when every new node maps to
-itself, shifts the state exactly by whole nodes, reproduces moments that are
-linear in x, and converges at second order for smooth fields."""
+itself, shifts the state exactly by whole nodes (also a curved chart moved
+with it), reproduces moments that are linear in x, clamps points past a wall
+to the wall node, and converges at second order for smooth fields."""
 import numpy as np
 import pytest
 
@@ -92,3 +93,46 @@ def test_trilinear_interpolation_converges_at_second_order():
         errs.append(np.abs(r - ref).max())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(rates - 2.0) < 0.1), (errs, rates)
+
+
+def test_whole_node_shift_on_a_curved_chart():
+    """A curved chart moved by one node along a periodic axis: the transition
+    map is psi(x) = x + e, D phi = J~(x)^-1 J(psi(x)) is the identity, and
+    every node takes the density and Cartesian velocity of the old node
+    x + e exactly (the old Jacobian is read at psi(x), not at x)."""
+    n = (6, 12, 8)
+    w = I.periodic_channel(n, 0.7, 0.05, 3, 0.06, 21, kmax=1, lmax=1)
+    ch0 = w["chart"]
+    roll = lambda a: np.roll(a.reshape(a.shape[:-1] + n[::-1]), -1, axis=-2).reshape(a.shape)  # y -> y + 1
+    g6n, dg18n, J9n = roll(ch0.g6), roll(ch0.dg18), roll(ch0.J9)
+    assert np.abs(J9n - ch0.J9).max() > 1e-3  # the chart varies along the shift
+    o = oracle.Lattice(n, w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+    o.set_metric(ch0.g6, ch0.dg18)
+    o.init()
+    o.step(10)
+    r0, v0 = o.moments(ch0.J9)
+    o.transform_interp(g6n, dg18n, ch0.J9, J9n, grid_psi(n, (0.0, 1.0, 0.0)))
+    r1, v1 = o.moments(J9n)
+    assert np.abs(r1 - roll(r0)).max() < 1e-13
+    assert np.abs(v1 - roll(v0)).max() < 1e-14
+    assert np.abs(v0).max() > 1e-3
+
+
+def test_points_beyond_a_wall_take_the_wall_node():
+    """A transition map that points past a non-periodic face is clamped to
+    the face: a node whose old point lies beyond the wall takes the wall
+    node's moments (the wall's velocity, here at rest)."""
+    n = (12, 6, 6)
+    g6, dg18, J9 = flat(n)
+    lo = (W, P, P)
+    o = oracle.Lattice(n, lo, lo, tau=0.8)
+    o.set_metric(g6, dg18)
+    x, y, z = I.grid(n)
+    o.init(1.0 + 0.01 * x, np.stack([0.02 + 0 * x, 0 * x, 0 * x]))
+    o.transform_interp(g6, dg18, J9, J9, grid_psi(n, (1.37, 0.0, 0.0)))
+    r, u = o.moments(J9)
+    beyond = x == n[0] - 2  # psi = n0 - 0.63 > n0 - 1
+    assert np.abs(u[0][beyond]).max() < 1e-15
+    assert np.abs(r[beyond] - (1.0 + 0.01 * (n[0] - 2))).max() < 1e-13  # the wall node carries its inner density
+    inside = x == n[0] - 3  # psi = n0 - 1.63: between the last fluid node and the wall
+    assert np.abs(u[0][inside] - 0.02 * (1 - 0.37) * (1.0 + 0.01 * (n[0] - 2)) / r[inside]).max() < 1e-13
