@@ -500,6 +500,24 @@ def dynamic_channel(n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6,
     return wl
 
 
+def developed_flow(n, umax, seed, layout=LAYOUT):
+    """A smooth initial state: the parabolic profile across the wall axis
+    along the flow axis everywhere, a 1e-3 density perturbation and a 1 %
+    velocity perturbation (seeded), so that relative errors of u are well
+    conditioned from the first step."""
+    rng = np.random.default_rng(seed)
+    w, _, fl = layout
+    r = np.stack(grid(n))
+    H = n[w] - 1
+    u = np.zeros(r.shape)
+    u[fl] = 4.0 * umax * r[w] * (H - r[w]) / H ** 2
+    ph = rng.uniform(0, 2 * np.pi, size=3)
+    bump = sum(np.sin(2 * np.pi * r[a] / n[a] + ph[a]) for a in range(3))
+    rho = 1.0 + 1e-3 * bump
+    u[fl] *= 1.0 + 0.01 * bump
+    return rho, u
+
+
 def dynamic_channel_at(w, t):
     """The chart and face velocities of a dynamic_channel workload at time t."""
     a, adot = time_law(t, w["period"])

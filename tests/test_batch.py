@@ -95,12 +95,11 @@ def test_full_batch_of_64_sampled_channels():
     developed-flow state (so that u is well conditioned), then the smallest,
     the largest and one more channel against the oracle over the whole
     channel, with mass."""
-    from windows import developed_flow
     ws = I.batch_channels(nb=64, seed0=4000)
     b = make_batch(ws)
     init = []
     for i, w in enumerate(ws):
-        rho0, u0 = developed_flow(w["n"], 0.05, 100 + i)
+        rho0, u0 = I.developed_flow(w["n"], 0.05, 100 + i)
         b[i].init_equilibrium(rho0, u0)
         init.append((rho0, u0))
     b.tune(reps=2)

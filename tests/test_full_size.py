@@ -98,14 +98,14 @@ def test_target_256_cube_sampled_windows():
     the outlet at the top wall); each window reproduces the whole run exactly
     on its core (tests/test_windows.py checks that on a small lattice)."""
     from paper_1803_07822_gb300.lattice import CurvedLattice
-    from windows import Window, developed_flow, oracle_cycle
+    from windows import Window, oracle_cycle
     b = _bench()
     spec = b.workload_spec("target256")
     n = spec["n"]
     w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
                           re=spec["re"])
     charts = b.snapshots(w, [500.0, 510.0])
-    rho0, u0 = developed_flow(n, w["umax"], 17)
+    rho0, u0 = I.developed_flow(n, w["umax"], 17)
     steps = (10, 10)
     R = 3 * sum(steps) + 2
     core = 6

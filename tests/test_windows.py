@@ -7,14 +7,14 @@ import numpy as np
 import pytest
 
 from paper_1803_07822_gb300 import inputs as I
-from windows import Window, developed_flow, oracle_cycle
+from windows import Window, oracle_cycle
 
 N3 = (36, 44, 34)
 K1, K2 = 1, 1
 
 
 def _run(n, bc_lo, bc_hi, tau, charts, win=None):
-    rho0, u0 = developed_flow(n, 0.04, 5)
+    rho0, u0 = I.developed_flow(n, 0.04, 5)
     return oracle_cycle(n, bc_lo, bc_hi, tau, charts, (K1, K2), win, rho0, u0)
 
 

@@ -98,21 +98,3 @@ def oracle_cycle(n, bc_lo, bc_hi, tau, charts, steps, win=None, rho0=None, u0=No
     faces(f1)
     o.step(steps[1])
     return o.moments(sel(c1.J9))
-
-
-def developed_flow(n, umax, seed, layout=(2, 0, 1)):
-    """A smooth initial state: the parabolic profile across the wall axis
-    along the flow axis everywhere, a 1e-3 density perturbation and a 1 %
-    velocity perturbation (seeded), so that relative errors of u are well
-    conditioned from the first step."""
-    rng = np.random.default_rng(seed)
-    w, _, fl = layout
-    r = np.stack(np.meshgrid(*(np.arange(n[a]) for a in (2, 1, 0)), indexing="ij")[::-1]).reshape(3, -1)
-    H = n[w] - 1
-    u = np.zeros((3, r.shape[1]))
-    u[fl] = 4.0 * umax * r[w] * (H - r[w]) / H ** 2
-    ph = rng.uniform(0, 2 * np.pi, size=3)
-    bump = sum(np.sin(2 * np.pi * r[a] / n[a] + ph[a]) for a in range(3))
-    rho = 1.0 + 1e-3 * bump
-    u[fl] *= 1.0 + 0.01 * bump
-    return rho, u
