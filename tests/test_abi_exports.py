@@ -105,3 +105,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_abi._build, "up_to_date", lambda: False)
     with pytest.raises(RuntimeError, match="nvcc"):
         _abi.load()
+
+
+def test_create_validates_before_touching_the_device():
+    """cslbm_create checks its arguments before any CUDA call: a null or
+    misaligned workspace is EINVAL, a short one ENOMEM, and nothing is
+    created (the pointer given is host memory and is never written)."""
+    lib = _abi.load()
+    p = _p3((16, 16, 8), (0, 0, 1), (0, 0, 1))
+    need = ctypes.c_size_t(0)
+    assert lib.cslbm_workspace_bytes(ctypes.byref(p), ctypes.byref(need)) == _abi.OK
+    out = ctypes.c_void_p(0)
+    buf = ctypes.create_string_buffer(1024 + 256)
+    base = (ctypes.addressof(buf) + 255) // 256 * 256
+    assert lib.cslbm_create(ctypes.byref(p), None, need.value, None, ctypes.byref(out)) == _abi.EINVAL
+    assert lib.cslbm_create(ctypes.byref(p), base + 8, need.value, None, ctypes.byref(out)) == _abi.EINVAL
+    assert b"256-byte" in lib.cslbm_last_error()
+    assert lib.cslbm_create(ctypes.byref(p), base, 1024, None, ctypes.byref(out)) == _abi.ENOMEM
+    assert out.value is None
+    p.tau = 0.4
+    assert lib.cslbm_create(ctypes.byref(p), base, need.value, None, ctypes.byref(out)) == _abi.EINVAL
