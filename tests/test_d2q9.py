@@ -134,3 +134,41 @@ def test_errors():
     g.step(3)
     r, u = g.moments()
     assert np.abs(r - 1).max() < 1e-6 and np.abs(u).max() < 1e-7
+
+
+def test_circular_couette_fp64():
+    """Circular Couette flow (Sec. V.B) on polar lattice coordinates (axis 0
+    radial between counter-rotating cylinders, radius ratio 1.063, axis 1
+    around them) through the D2Q9 path in FP64: against the 2-D oracle, and
+    the azimuthal profile against the analytic A r + B / r."""
+    from paper_1803_07822_gb300.lattice import CurvedLattice2D
+    m, ny, tau = 17, 4, 1.0
+    L = m - 1
+    r0 = L / 0.063
+    n = (m, ny)
+    ch = I.annulus_chart2d(n, r0)
+    g = CurvedLattice2D(n, (1, 0), (1, 0), tau=tau, storage="fp64")
+    g.set_chart(ch)
+    o = oracle.Lattice2D(n, (1, 0), (1, 0), tau=tau)
+    o.set_metric(ch.g3, ch.dg6)
+    om1 = 1e-3 / r0
+    om2 = -om1
+    for side, om in ((0, om1), (1, om2)):
+        u = np.stack([np.zeros(ny), np.full(ny, om * r0)])  # u^1 = v_theta r0 / r
+        g.set_boundary_velocity(0, side, u)
+        o.set_face_velocity(0, side, u)
+    g.init_equilibrium()
+    o.init()
+    steps = int(4 * L ** 2 * 6)
+    g.step(steps)
+    o.step(steps)
+    rg, vg = g.moments(cartesian=True)
+    ro, vo = o.moments(ch.J4)
+    assert rel(rg, ro) < 1e-12 and rel(vg, vo) < 1e-9, (rel(rg, ro), rel(vg, vo))
+    x, y = I.grid2d(n)
+    r, th = r0 + x, y / r0
+    R1, R2 = r0, r0 + L
+    A = (om2 * R2 ** 2 - om1 * R1 ** 2) / (R2 ** 2 - R1 ** 2)
+    B = (om1 - om2) * R1 ** 2 * R2 ** 2 / (R2 ** 2 - R1 ** 2)
+    vt = -np.sin(th) * vg[0] + np.cos(th) * vg[1]
+    assert rel(vt, A * r + B / r) < 5e-6
