@@ -352,29 +352,40 @@ typedef struct {
 } cslbm2d_params;
 typedef struct cslbm2d_ctx cslbm2d_ctx;
 
+/* Device workspace bytes (EINVAL for invalid parameters or FP16/BF16
+ * storage); create in a caller-owned, 256-byte aligned workspace (ENOMEM when
+ * short), destroy (never frees caller memory). */
 cslbm_status cslbm2d_workspace_bytes(const cslbm2d_params* p, size_t* bytes);
 cslbm_status cslbm2d_create(const cslbm2d_params* p, void* workspace, size_t bytes, void* stream, cslbm2d_ctx** out);
 cslbm_status cslbm2d_destroy(cslbm2d_ctx* ctx);
 /* geometry (App. A in 2-D: g^ij, sqrt(g), Gamma) from g and dg; EINVAL when g
  * is not positive definite somewhere (synchronises) */
 cslbm_status cslbm2d_set_metric(cslbm2d_ctx* ctx, const double* g3, const double* dg6, int on_device);
+/* the chart's Jacobian J4 [4][N] for Cartesian readout and wall forces
+ * (Sec. IV.A, vector transformation between the lattice and Cartesian space) */
 cslbm_status cslbm2d_set_jacobian(cslbm2d_ctx* ctx, const double* J4, int on_device);
 /* chart change: new geometry and the node-wise transformation of f and of
  * the forcing history (Sec. IV.B) */
 cslbm_status cslbm2d_update_metric(cslbm2d_ctx* ctx, const double* g3, const double* dg6, const double* Jnew4,
                                    int on_device);
+/* velocity imposed on a wall or inflow face (Sec. V, boundary nodes on the
+ * wall), u2 [2][n of the other axis], contravariant; EINVAL on a periodic face */
 cslbm_status cslbm2d_set_boundary_velocity(cslbm2d_ctx* ctx, int axis, int side, const double* u2, int on_device);
-/* f = f^eq(rho, u; g), F(-dt) := F(0); rho [N] and u2 [2][N] (contravariant)
- * may be null for 1 and 0 */
+/* f = f^eq(rho, u; g) (App. B, equilibrium coefficients), F(-dt) := F(0);
+ * rho [N] and u2 [2][N] (contravariant) may be null for 1 and 0; ESTATE
+ * before the metric is set */
 cslbm_status cslbm2d_init_equilibrium(cslbm2d_ctx* ctx, const double* rho, const double* u2, int on_device);
-/* nsteps LBM steps (two kernels each), asynchronous */
+/* nsteps LBM steps (Sec. II, Eqs. collision and streaming, with the forcing
+ * of Eqs. forcing-A/B/C), two kernels each, asynchronous; ESTATE before
+ * init_equilibrium */
 cslbm_status cslbm2d_step(cslbm2d_ctx* ctx, int nsteps);
-/* rho [N], u2 [2][N] (contravariant, or Cartesian v = J u) of the state with
- * the boundary rule applied; synchronises */
+/* rho [N], u2 [2][N] (Sec. II, Eqs. fields: contravariant, or Cartesian
+ * v = J u) of the state with the boundary rule applied; synchronises */
 cslbm_status cslbm2d_get_moments(cslbm2d_ctx* ctx, double* rho, double* u2, int cartesian, int on_device);
-/* FP64 sum of sqrt(g) rho; synchronises */
+/* FP64 sum of sqrt(g) rho (the mass of Sec. V.B); synchronises */
 cslbm_status cslbm2d_total_mass(cslbm2d_ctx* ctx, double* out);
-/* force of the fluid on face (axis, side), s sum J T^{i axis} sqrt(g) per unit depth, FP64; synchronises */
+/* force of the fluid on face (axis, side), s sum J T^{i axis} sqrt(g) per unit
+ * depth (Sec. IV.A, momentum exchange on the nodes), FP64; synchronises */
 cslbm_status cslbm2d_wall_force(cslbm2d_ctx* ctx, int axis, int side, double out2[2]);
 
 const char* cslbm_last_error(void);
