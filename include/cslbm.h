@@ -119,7 +119,9 @@ cslbm_status cslbm_set_jacobian(cslbm_ctx* ctx, const double* J9, int on_device)
  * a_(1) -> D phi a_(1), Pi -> D phi Pi D phi^T (or a_(2) itself, see
  * transform_flags), recomposed to second order with the new sqrt(g).  The
  * history's A, B, C transform as scalar, vector and rank-2 tensor.  Jnew
- * becomes the current Jacobian. */
+ * becomes the current Jacobian.  ESTATE before cslbm_init_equilibrium.  A
+ * metric with det g <= 0 somewhere is flagged on the device and reported as
+ * EINVAL by the next cslbm_check (the call itself does not synchronise). */
 cslbm_status cslbm_update_metric(cslbm_ctx* ctx, const double* g6, const double* dg18,
                                  const double* Jnew9, int on_device);
 
@@ -139,28 +141,37 @@ cslbm_status cslbm_set_boundary_velocity(cslbm_ctx* ctx, int axis, int side, con
  * collision (Eq. collision) and streaming (Eq. streaming), with the Hermite
  * equilibrium (App. B), the forcing of Eqs. forcing2 / forcing-A/B/C with the
  * trapezoidal history, the isotropic lattice gradient of App. D and the
- * boundary rule.  Asynchronous. */
+ * boundary rule.  Asynchronous.  ESTATE before cslbm_init_equilibrium, EINVAL
+ * for nsteps < 0. */
 cslbm_status cslbm_step(cslbm_ctx* ctx, int nsteps);
 
 /* Density and velocity (Eqs. fields1/2): rho [N], u3 [3][N], FP64;
- * contravariant u^i, or Cartesian v^a = J^a_i u^i when cartesian != 0. */
+ * contravariant u^i, or Cartesian v^a = J^a_i u^i when cartesian != 0.
+ * ESTATE before cslbm_init_equilibrium.  Synchronises for host outputs. */
 cslbm_status cslbm_get_moments(cslbm_ctx* ctx, double* rho, double* u3, int cartesian,
                                int on_device);
 
-/* Total mass sum_x sqrt(g) rho (volume element of App. A), FP64. Syncs. */
+/* Total mass sum_x sqrt(g) rho (volume element of App. A), FP64. Syncs.
+ * ESTATE before cslbm_init_equilibrium. */
 cslbm_status cslbm_total_mass(cslbm_ctx* ctx, double* out);
 
 /* Force of the fluid on the face (axis, side), Cartesian, FP64 (Sec. IV.A
  * force coupling):  F^a = s sum_nodes J^a_i T^{i axis} sqrt(g), s = -1 for
- * the low face and +1 for the high face, T of Eq. fields3. Syncs. */
+ * the low face and +1 for the high face, T of Eq. fields3. Syncs.  ESTATE
+ * before cslbm_init_equilibrium, EINVAL for a bad face. */
 cslbm_status cslbm_wall_force(cslbm_ctx* ctx, int axis, int side, double out3[3]);
 
 /* Non-finite or supersonic (|u|^2 g > 0.3^2 in lattice units) state?
- * Returns CSLBM_EUNSTABLE if so, CSLBM_OK otherwise. Syncs. */
+ * Returns CSLBM_EUNSTABLE if so, CSLBM_OK otherwise.  Also reports, first,
+ * a pending det g <= 0 flag of cslbm_update_metric (EINVAL) and a bounded
+ * wait of the row-staged or fused step pass that ran out (ETIMEOUT; the
+ * pass's counters are reset).  ESTATE before cslbm_init_equilibrium. Syncs. */
 cslbm_status cslbm_check(cslbm_ctx* ctx);
 
 /* Checkpoint: the bytes of the evolving state (distributions + forcing
- * history), copied to/from `buf` (device or host per on_device). */
+ * history), copied to/from `buf` (device or host per on_device).  EINVAL for a
+ * buffer smaller than cslbm_state_bytes; saving needs a state (ESTATE), and
+ * loading one gives the context a state. */
 cslbm_status cslbm_state_bytes(const cslbm_ctx* ctx, size_t* bytes);
 cslbm_status cslbm_save_state(cslbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 cslbm_status cslbm_load_state(cslbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
@@ -192,7 +203,6 @@ cslbm_status cslbm_profile_read(cslbm_ctx* ctx, double* step_ms, long long* nste
  * the context's stream. */
 cslbm_status cslbm_total_mass_static(cslbm_ctx* ctx, double* out);
 
-/* Message of the last failure on this thread ("" if none). */
 /* ---------------------------------------------------------------------------
  * Adjoint: gradients of a wall force with respect to the geometry (FP32 or
  * FP64 storage; periodic faces and walls at rest; static metric; state
@@ -388,6 +398,7 @@ cslbm_status cslbm2d_total_mass(cslbm2d_ctx* ctx, double* out);
  * depth (Sec. IV.A, momentum exchange on the nodes), FP64; synchronises */
 cslbm_status cslbm2d_wall_force(cslbm2d_ctx* ctx, int axis, int side, double out2[2]);
 
+/* Message of the last failure on this thread ("" if none). */
 const char* cslbm_last_error(void);
 
 #ifdef __cplusplus
