@@ -833,14 +833,22 @@ def main():
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        grad_cpu, trans_cpu = oracle_side_samples(spec)
-        line["lattice_gradient"]["cpu_baseline"] = grad_cpu
-        line["transform_interp"]["cpu_baseline"] = trans_cpu
         mlups, secs, n, cores = oracle_cycle_sample(spec, 2, 0)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, 2 cycles "
                                           f"(transform + {STEPS_PER_CYCLE} steps + reductions), FP64",
-                                "cpu": cpu_model(), "single_thread": oracle_single_thread()}
+                                "cpu": cpu_model()}
+        # secondary oracle timings: a failure is reported in the line, not raised
+        try:
+            line["cpu_baseline"]["single_thread"] = oracle_single_thread()
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline"]["single_thread"] = {"error": str(e)[-300:]}
+        try:
+            grad_cpu, trans_cpu = oracle_side_samples(spec)
+            line["lattice_gradient"]["cpu_baseline"] = grad_cpu
+            line["transform_interp"]["cpu_baseline"] = trans_cpu
+        except Exception as e:  # noqa: BLE001
+            line["lattice_gradient"]["cpu_baseline"] = {"error": str(e)[-300:]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
