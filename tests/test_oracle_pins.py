@@ -91,6 +91,7 @@ def _charts():
     dfm = I.fourier_deformation(n, 4, 0.08, seed=12, flow_periodic=False)
     yield I.channel_chart(n, dfm)
     yield I.reparam_chart(n, 0.1)
+    yield I.annulus_chart(n, 6.0)  # polar coordinates: Gamma^r_tt and Gamma^t_rt nonzero
 
 
 @pytest.mark.parametrize("chart", list(_charts()))
@@ -189,3 +190,30 @@ def test_forcing_flat_reduces_to_body_force():
     assert abs(A) < 1e-15 and np.abs(C).max() < 1e-14 and np.allclose(B, fext, atol=1e-15)
     F = oracle.forcing_recompose(A, B, C, 1.0)
     assert np.allclose(F, w * (c @ fext) / CS2, atol=1e-14)
+
+
+def test_annulus_chart_derivatives():
+    """The polar chart's J and second derivatives are those of h(x, y, z) =
+    ((r0 + x) cos(y/r0), (r0 + x) sin(y/r0), z): central differences of h
+    (step 1e-4) at the nodes."""
+    n, r0, e = (5, 7, 3), 6.0, 1e-4
+    ch = I.annulus_chart(n, r0)
+    x, y, z = I.grid(n)
+
+    def h(x, y, z):
+        return np.stack([(r0 + x) * np.cos(y / r0), (r0 + x) * np.sin(y / r0), z])
+
+    X = [x, y, z]
+    for i in range(3):
+        d = [0.0, 0.0, 0.0]
+        d[i] = e
+        col = (h(*(X[k] + d[k] for k in range(3))) - h(*(X[k] - d[k] for k in range(3)))) / (2 * e)
+        for a in range(3):
+            assert np.abs(ch.J9[a * 3 + i] - col[a]).max() < 1e-8
+            for j in range(3):
+                dj = [0.0, 0.0, 0.0]
+                dj[j] = e
+                Jp = (h(*(X[k] + d[k] + dj[k] for k in range(3))) - h(*(X[k] - d[k] + dj[k] for k in range(3))))
+                Jm = (h(*(X[k] + d[k] - dj[k] for k in range(3))) - h(*(X[k] - d[k] - dj[k] for k in range(3))))
+                second = (Jp - Jm) / (4 * e * e)
+                assert np.abs(ch.hess[a * 9 + i * 3 + j] - second[a]).max() < 1e-5
