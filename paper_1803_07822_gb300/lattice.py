@@ -362,25 +362,34 @@ class CurvedLattice2D:
         call("cslbm2d_create", ctypes.byref(self.params), self.workspace.data_ptr(), nb.value,
              self.stream.cuda_stream, ctypes.byref(self.ctx))
 
-    def _arg(self, a, rows):
+    def _arg(self, a, count):
+        """(pointer, on_device, keep-alive) for an FP64 input of `count` values
+        (a CUDA tensor stays on the device; anything else is a host array)."""
         if a is None:
             return None, 1, None
         torch = _torch()
         if isinstance(a, torch.Tensor):
-            t = a.to(self.device, torch.float64).contiguous()
-            return t.data_ptr(), 1, t
+            if a.device.type != "cuda":
+                a = a.detach().to(torch.float64).contiguous().numpy()
+            else:
+                t = a.detach().to(self.device, torch.float64).contiguous()
+                if t.numel() != count:
+                    raise ValueError(f"expected {count} values, got {t.numel()}")
+                return t.data_ptr(), 1, t
         h = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+        if h.size != count:
+            raise ValueError(f"expected {count} values, got {h.size}")
         return h.ctypes.data, 0, h
 
     def set_metric(self, g3, dg6):
-        p1, d1, k1 = self._arg(g3, 3)
-        p2, d2, k2 = self._arg(dg6, 6)
+        p1, d1, k1 = self._arg(g3, 3 * self.N)
+        p2, d2, k2 = self._arg(dg6, 6 * self.N)
         if d1 != d2:
             raise ValueError("g3 and dg6 must both be host or both device arrays")
         call("cslbm2d_set_metric", self.ctx, p1, p2, d1)
 
     def set_jacobian(self, J4):
-        p, d, k = self._arg(J4, 4)
+        p, d, k = self._arg(J4, 4 * self.N)
         call("cslbm2d_set_jacobian", self.ctx, p, d)
 
     def set_chart(self, chart):
@@ -388,22 +397,22 @@ class CurvedLattice2D:
         self.set_jacobian(chart.J4)
 
     def update_metric(self, g3, dg6, J4):
-        p1, d1, k1 = self._arg(g3, 3)
-        p2, d2, k2 = self._arg(dg6, 6)
-        p3, d3, k3 = self._arg(J4, 4)
+        p1, d1, k1 = self._arg(g3, 3 * self.N)
+        p2, d2, k2 = self._arg(dg6, 6 * self.N)
+        p3, d3, k3 = self._arg(J4, 4 * self.N)
         if not (d1 == d2 == d3):
             raise ValueError("metric inputs must all be host or all device arrays")
         call("cslbm2d_update_metric", self.ctx, p1, p2, p3, d1)
 
     def set_boundary_velocity(self, axis, side, u2):
-        p, d, k = self._arg(u2, 2)
+        p, d, k = self._arg(u2, 2 * self.n[1 - int(axis)]) if 0 <= int(axis) <= 1 else (None, 1, None)
         call("cslbm2d_set_boundary_velocity", self.ctx, int(axis), int(side), p, d)
         self._keep_face = getattr(self, "_keep_face", {})
         self._keep_face[(axis, side)] = k
 
     def init_equilibrium(self, rho=None, u=None):
-        p1, d1, k1 = self._arg(rho, 1)
-        p2, d2, k2 = self._arg(u, 2)
+        p1, d1, k1 = self._arg(rho, self.N)
+        p2, d2, k2 = self._arg(u, 2 * self.N)
         on_dev = d1 if rho is not None else d2
         call("cslbm2d_init_equilibrium", self.ctx, p1, p2, on_dev)
 
