@@ -132,6 +132,7 @@ class CurvedLattice:
         out = torch.empty((3, ncomp, self.N), dtype=torch.float64, device=self.device)
         call("cslbm_lattice_gradient", self.ctx, f.data_ptr(), ncomp, int(order), out.data_ptr(), scratch.data_ptr(),
              scratch.numel())
+        self._keep = (f, scratch)  # alive until the stream has used them
         return out
 
     def _metric_scratch(self, order):
@@ -145,6 +146,7 @@ class CurvedLattice:
         g = self._dev64(g6, 6)
         scratch = self._metric_scratch(order)
         call("cslbm_set_metric_lattice", self.ctx, g.data_ptr(), int(order), scratch.data_ptr(), scratch.numel())
+        self._keep = (g, scratch)  # alive until the stream has used them
 
     def update_metric_lattice(self, g6, J9, order=4):
         """update_metric (metric change + transformation) with dg from g6 on the lattice."""
@@ -153,6 +155,7 @@ class CurvedLattice:
         scratch = self._metric_scratch(order)
         call("cslbm_update_metric_lattice", self.ctx, g.data_ptr(), J.data_ptr(), int(order), scratch.data_ptr(),
              scratch.numel())
+        self._keep = (g, J, scratch)  # alive until the stream has used them
 
     def set_chart(self, chart):
         """Metric and Jacobian of an inputs.Chart (no transformation)."""
