@@ -112,7 +112,14 @@ class CurvedLattice:
         scratch = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
         call("cslbm_update_metric_interp", self.ctx, g.data_ptr(), d.data_ptr(), J.data_ptr(), ps.data_ptr(),
              scratch.data_ptr(), scratch.numel())
-        self._keep = (g, d, J, ps, scratch)  # alive until the stream has used them
+        self._hold(g, d, J, ps, scratch)
+
+    def _hold(self, *tensors):
+        """Device buffers an asynchronous call reads: marked as used on the
+        context's stream, so that the allocator does not hand their memory out
+        again before that stream has run the call."""
+        for t in tensors:
+            t.record_stream(self.stream)
 
     # -- lattice derivatives (App. D) ----------------------------------------
     def _dev64(self, a, rows):
@@ -132,7 +139,7 @@ class CurvedLattice:
         out = torch.empty((3, ncomp, self.N), dtype=torch.float64, device=self.device)
         call("cslbm_lattice_gradient", self.ctx, f.data_ptr(), ncomp, int(order), out.data_ptr(), scratch.data_ptr(),
              scratch.numel())
-        self._keep = (f, scratch)  # alive until the stream has used them
+        self._hold(f, scratch)
         return out
 
     def _metric_scratch(self, order):
@@ -146,7 +153,7 @@ class CurvedLattice:
         g = self._dev64(g6, 6)
         scratch = self._metric_scratch(order)
         call("cslbm_set_metric_lattice", self.ctx, g.data_ptr(), int(order), scratch.data_ptr(), scratch.numel())
-        self._keep = (g, scratch)  # alive until the stream has used them
+        self._hold(g, scratch)
 
     def update_metric_lattice(self, g6, J9, order=4):
         """update_metric (metric change + transformation) with dg from g6 on the lattice."""
@@ -155,7 +162,7 @@ class CurvedLattice:
         scratch = self._metric_scratch(order)
         call("cslbm_update_metric_lattice", self.ctx, g.data_ptr(), J.data_ptr(), int(order), scratch.data_ptr(),
              scratch.numel())
-        self._keep = (g, J, scratch)  # alive until the stream has used them
+        self._hold(g, J, scratch)
 
     def set_chart(self, chart):
         """Metric and Jacobian of an inputs.Chart (no transformation)."""
