@@ -70,6 +70,7 @@ class CurvedLattice:
                 t = a.detach().to(self.device, torch.float64).contiguous()
                 if t.numel() != rows:
                     raise ValueError(f"expected {rows} values, got {t.numel()}")
+                t.record_stream(self.stream)  # a converted copy may be read after this call returns
                 return t.data_ptr(), 1, t
         h = np.ascontiguousarray(a, dtype=np.float64)
         if h.size != rows:
@@ -385,6 +386,7 @@ class CurvedLattice2D:
                 t = a.detach().to(self.device, torch.float64).contiguous()
                 if t.numel() != count:
                     raise ValueError(f"expected {count} values, got {t.numel()}")
+                t.record_stream(self.stream)  # a converted copy may be read after this call returns
                 return t.data_ptr(), 1, t
         h = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
         if h.size != count:
