@@ -11,7 +11,7 @@ import pytest
 import oracle
 from paper_1803_07822_gb300 import inputs as I
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late]
 P, W = oracle.PERIODIC, oracle.WALL
 HERE = os.path.dirname(os.path.abspath(__file__))
 CC = json.load(open(os.path.join(HERE, "golden", "paper_bounds.json")))["couette"]

@@ -136,6 +136,7 @@ def test_errors():
     assert np.abs(r - 1).max() < 1e-6 and np.abs(u).max() < 1e-7
 
 
+@pytest.mark.late
 def test_circular_couette_fp64():
     """Circular Couette flow (Sec. V.B) on polar lattice coordinates (axis 0
     radial between counter-rotating cylinders, radius ratio 1.063, axis 1

@@ -3,7 +3,7 @@ bench.py times, against the oracle: over the whole field, one cycle of the
 128 x 128 x 256 dynamic channel (chart change with transformation, face
 velocities, 10 steps through the default step pass, mass and wall force) and
 5 steps of the 4096 x 1024 D2Q9 channel.  The 256^3 channel and the full
-64-channel batch are in test_zy_full_size_sampled.py."""
+64-channel batch are in test_full_size_sampled.py."""
 import importlib.util
 import os
 

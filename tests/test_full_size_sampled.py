@@ -1,4 +1,4 @@
-"""The heaviest full-size parity tests, run after the others: the 256^3
+"""The heaviest full-size parity tests (marked late: run after the others): the 256^3
 deformed channel through one bench cycle in FP32, FP16 and BF16 storage
 against the oracle on sampled windows (tests/windows.py), and the benchmark's
 64-channel batch in its launch configuration against the oracle on three
@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_1803_07822_gb300 import inputs as I
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.late]
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
