@@ -6,7 +6,8 @@ allocator, a plugin whose framework owns all allocations).  Its partial sums
 live in a fixed device array instead of the context's workspace.  Checked
 through the C ABI against cslbm_total_mass on two calls in a row, on two
 lattices, so that the second call runs on the array the first one left.
-This file is collected last.
+This file is collected after the other files; only tests marked late run
+after it.
 """
 import ctypes
 
