@@ -289,6 +289,29 @@ def cpu_model(path="/proc/cpuinfo"):
     return f"{platform.machine()}, implementer {imp.group(1) if imp else '?'}, part {part.group(1) if part else '?'}"
 
 
+def oracle_batch_sample(ws, count=3, steps=10):
+    """The FP64 oracle on the `count` smallest channels of a batch, one after
+    another (as the per-channel form runs them), `steps` steps each after 2.
+    Returns the cpu_baseline object."""
+    import oracle
+    order = sorted(range(len(ws)), key=lambda i: int(np.prod(ws[i]["n"])))[:count]
+    nodes, secs = 0, 0.0
+    for i in order:
+        w = ws[i]
+        o = oracle.Lattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+        o.set_metric(w["chart"].g6, w["chart"].dg18)
+        o.init()
+        o.step(2)
+        t0 = time.perf_counter()
+        o.step(steps)
+        secs += time.perf_counter() - t0
+        nodes += int(np.prod(w["n"]))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nodes * steps / secs / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the {count} smallest channels of the batch ({nodes} nodes), {steps} steps each after 2, "
+                      f"FP64 ({secs:.1f} s)"}
+
+
 def bench_batch(args):
     """The batched form: 64 independent periodic channels with sides drawn from
     U{32..96} per axis, 4-mode deformations of 2-10 % amplitude, tau in
@@ -372,6 +395,11 @@ def bench_batch(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_batch_sample(ws)
+        except Exception as e:  # noqa: BLE001
+            line["cpu_baseline"] = {"error": str(e)[-300:]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -77,3 +77,11 @@ def test_side_report_oracle_samples():
     g, t = b.oracle_side_samples(b.workload_spec("crop64"))
     assert g["kind"] == "oracle" and g["value"] > 0 and g["unit"] == "Mnode/s" and "32x64x32" in g["sample"]
     assert t["kind"] == "oracle" and t["node_wise_ms"] > 0 and t["interp_ms"] > 0 and t["nodes"] == 32 * 64 * 32
+
+
+def test_batch_oracle_sample():
+    from paper_1803_07822_gb300 import inputs as I
+    b = _bench()
+    ws = I.batch_channels(nb=4, seed0=4100, side=(8, 12), kmax=1, lmax=1)
+    d = b.oracle_batch_sample(ws, count=2, steps=2)
+    assert d["kind"] == "oracle" and d["value"] > 0 and "2 smallest channels" in d["sample"]
