@@ -433,6 +433,11 @@ def bench_side(args):
                     value=r["roofline"]["achieved"], unit="GFLOP/s", higher_is_better=True, dtype="f64",
                     ms_per_step=r["ms"], config={"workload": "six metric fields of the 128x128x256 dynamic channel"},
                     lattice_gradient=r)
+        if not args.no_cpu_baseline:
+            try:
+                r["cpu_baseline"] = oracle_side_samples(workload_spec("dynamic"))[0]
+            except Exception as e:  # noqa: BLE001
+                r["cpu_baseline"] = {"error": str(e)[-300:]}
     print(json.dumps(line), flush=True)
 
 
