@@ -8,8 +8,7 @@ expansion, App. B; lattice gradient, App. D; transformation, Sec. IV.B).
 
 Parity unpinned (no printed value to match; held only by convergence and
 invariant tests): the sqrt(g) factor on the non-equilibrium part of the wall
-rule, the Gamma rho u part of the covariant derivative inside the forcing
-moment C, and the transformation variants.
+rule.
 """
 from __future__ import annotations
 
@@ -54,7 +53,8 @@ def _load():
                          "orc_feq", "orc_forcing_recompose", "orc_forcing_moments",
                          "orc_lattice", "orc_lattice_gradient", "orc_lattice_laplacian",
                          "orc_transform_interp", "o2_lattice", "o2_geometry", "o2_init", "o2_step",
-                         "o2_moments", "o2_mass", "o2_wall_force", "o2_transform", "o2_forcing_recompose"):
+                         "o2_moments", "o2_mass", "o2_wall_force", "o2_transform", "o2_forcing_recompose",
+                         "o2_forcing_moments"):
                 getattr(_lib, name).restype = ctypes.c_int
     return _lib
 
@@ -308,6 +308,18 @@ def forcing_recompose2d(A, B2, C4, sqrtg):
     Bk, Ck = _f64(B2, (2,)), _f64(C4, (4,))
     _load().o2_forcing_recompose(ctypes.c_double(A), _p(Bk), _p(Ck), ctypes.c_double(sqrtg), _p(out))
     return out
+
+
+def forcing_moments2d(j2, T4, Dj4, ginv4, gam8, theta=1.0 / 3.0, fext2=(0, 0)):
+    """A, B^i, C^ij (Eqs. forcing-A/B/C in 2-D) for one node; Dj4[k*2+i] = d_k(rho u^i)."""
+    args = [_f64(x) for x in (j2, T4, Dj4, ginv4, gam8)]
+    fe = _f64(fext2)
+    A = ctypes.c_double(0.0)
+    B = np.zeros(2)
+    C = np.zeros(4)
+    _load().o2_forcing_moments(*[_p(a) for a in args], ctypes.c_double(theta), _p(fe), ctypes.byref(A), _p(B),
+                               _p(C))
+    return A.value, B, C
 
 
 def geometry2d(n, g3, dg6):

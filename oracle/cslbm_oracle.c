@@ -39,8 +39,11 @@
  *
  * Parity unpinned (no printed value to match; held by convergence and
  * invariant tests only): the sqrt(g) factor on the non-equilibrium part of the
- * wall and inflow rule, the Gamma rho u part of the covariant derivative inside
- * the forcing moment C, and the literal-a2 transformation variant.
+ * wall and inflow rule.  The Gamma rho u part of the covariant derivative
+ * inside the forcing moment C is pinned by a parallel field of flat space
+ * (a uniform Cartesian flow in a curved chart, whose covariant derivative
+ * vanishes); the literal-a2 transformation by its tensor rule under a stretch
+ * and a shear.
  */
 #include <math.h>
 #include <stdlib.h>

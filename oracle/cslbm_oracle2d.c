@@ -22,9 +22,10 @@
  *   face (axis, side): [2][n of the other axis], contravariant, NULL = 0.
  *
  * Parity unpinned, as in three dimensions: the sqrt(g) factor on the
- * non-equilibrium part of the wall and inflow rule and the Gamma rho u part of
- * the covariant derivative inside C (held by convergence and invariant tests
- * only).
+ * non-equilibrium part of the wall and inflow rule (held by convergence and
+ * invariant tests only).  The Gamma rho u part of the covariant derivative
+ * inside C is pinned, as in three dimensions, by a uniform Cartesian flow in
+ * polar coordinates, whose covariant derivative vanishes.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -322,6 +323,23 @@ int o2_forcing_recompose(double A, const double *B2, const double *C4, double sg
 {
     const double B[2] = {B2[0], B2[1]}, C[2][2] = {{C4[0], C4[1]}, {C4[2], C4[3]}};
     forcing2(A, B, C, sg, out9);
+    return 0;
+}
+
+/* A, B^i, C^ij of one node: j2 = rho u^i, T4 = T^ij, Dj4[k*2+i] = d_k(rho u^i),
+ * ginv4 = g^ij, gam8 = Gamma^i_jk at (i*4 + j*2 + k); outputs A, B2, C4 (full 2 x 2) */
+int o2_forcing_moments(const double *j2, const double *T4, const double *Dj4, const double *ginv4,
+                       const double *gam8, double theta, const double *fext2, double *A, double *B2, double *C4)
+{
+    double T[2][2], Dj[2][2], gi[2][2], gam[2][2][2], C[2][2];
+    for (int a = 0; a < 4; a++) {
+        T[a / 2][a % 2] = T4[a];
+        Dj[a / 2][a % 2] = Dj4[a];
+        gi[a / 2][a % 2] = ginv4[a];
+    }
+    for (int a = 0; a < 8; a++) gam[a / 4][(a / 2) % 2][a % 2] = gam8[a];
+    forcing_moments2(j2, T, Dj, gi, gam, theta, fext2, A, B2, C);
+    for (int a = 0; a < 4; a++) C4[a] = C[a / 2][a % 2];
     return 0;
 }
 

@@ -286,3 +286,30 @@ def test_chart_change_keeps_density_and_cartesian_velocity():
     assert np.abs(r1 - r0)[fluid].max() < 1e-13
     assert np.abs(v1 - v0)[:, fluid].max() < 1e-14
     assert np.abs(c1.J4 - c0.J4).max() > 0.01  # the charts differ
+
+
+def test_forcing_C_parallel_field_has_no_theta_part_2d():
+    """As in three dimensions: a uniform Cartesian flow in polar coordinates
+    is a parallel field (nabla_k j^i = d_k j^i + Gamma^i_kl j^l = 0), so the
+    theta part of C^ij (Eq. forcing-C) vanishes and C does not depend on theta;
+    without the Gamma rho u term it would."""
+    n = (7, 9)
+    ch = I.annulus_chart2d(n, 5.0)
+    N = int(np.prod(n))
+    sg, gi, gam = oracle.geometry2d(n, ch.g3, ch.dg6)
+    J = np.moveaxis(ch.J4.reshape(2, 2, N), 2, 0)
+    Jinv = np.linalg.inv(J)
+    dJ = np.moveaxis(ch.hess.reshape(2, 2, 2, N), 3, 0)  # [n, b, m, k] = d_k J^b_m
+    rng = np.random.default_rng(22)
+    worst, scale = 0.0, 0.0
+    for v in rng.choice(N, size=10, replace=False):
+        j = Jinv[v] @ (0.05 * rng.standard_normal(2))
+        Dj = -np.einsum("ib,bmk,m->ki", Jinv[v], dJ[v], j)
+        T = rng.standard_normal((2, 2))
+        T = T + T.T
+        C = [oracle.forcing_moments2d(j, T.ravel(), Dj.ravel(), gi[:, v], gam[:, v], th)[2] for th in (1 / 3, 0.25)]
+        C0 = [oracle.forcing_moments2d(j, T.ravel(), Dj.ravel(), gi[:, v], np.zeros(8), th)[2] for th in (1 / 3, 0.25)]
+        worst = max(worst, np.abs(C[0] - C[1]).max())
+        scale = max(scale, np.abs(C0[0] - C0[1]).max())
+    assert scale > 1e-4
+    assert worst < 1e-15 + 1e-12 * scale, (worst, scale)

@@ -49,6 +49,18 @@ CASES = [
      "T[a][b] += (fe[l] + (1.0 - 1.0 / p->tau) * (fl - fe[l])) * CV[l][a] * CV[l][b] * sg;\n        }\n"
      "        for (int a = 0; a < 3; a++)\n            for (int i = 0; i < 3; i++) acc[a]",
      "test_oracle_boundary.py::test_flat_couette_wall_force_is_the_exact_stress"),
+    ("nabla_k rho u^i without Gamma^i_kl rho u^l", SRC3,
+     "for (int l = 0; l < 3; l++) s += gam[i][k][l] * j[l];",
+     "for (int l = 0; l < 3; l++) s += 0.0 * gam[i][k][l] * j[l];",
+     "test_oracle_pins.py::test_forcing_C_parallel_field_has_no_theta_part"),
+    ("nabla_k rho u^i with Gamma^l_ki rho u^l", SRC3,
+     "for (int l = 0; l < 3; l++) s += gam[i][k][l] * j[l];",
+     "for (int l = 0; l < 3; l++) s += gam[l][k][i] * j[l];",
+     "test_oracle_pins.py::test_forcing_C_parallel_field_has_no_theta_part"),
+    ("literal-a2 transform subtracting c_s^2 rho delta twice", SRC3,
+     "t2[i][j] = tM[i][j] - (p->literal_a2 ? 0.0 : CS2 * a0 * (i == j));",
+     "t2[i][j] = tM[i][j] - CS2 * a0 * (i == j);",
+     "test_oracle_step.py::test_transform_literal_mode_under_stretch_and_shear"),
     ("2-D outflow copy without sqrt(g) ratio", SRC2,
      "for (int l = 0; l < Q2; l++) fout[l * N + v] = fin[l * N + vi] * sgi / sgw;",
      "for (int l = 0; l < Q2; l++) fout[l * N + v] = fin[l * N + vi];",
@@ -56,6 +68,10 @@ CASES = [
     ("2-D b2 without -c_s^2 delta A", SRC2,
      "b2[a][b] = C[a][b] - CS2_2 * (a == b) * A;", "b2[a][b] = C[a][b];",
      "test_oracle2d.py::test_forcing_recomposition_moments_2d"),
+    ("2-D nabla_k rho u^i without Gamma^i_kl rho u^l", SRC2,
+     "for (int l = 0; l < 2; l++) s += gam[i][k][l] * j[l];",
+     "for (int l = 0; l < 2; l++) s += 0.0 * gam[i][k][l] * j[l];",
+     "test_oracle2d.py::test_forcing_C_parallel_field_has_no_theta_part_2d"),
     ("2-D transform with J J~^-1 for J~^-1 J", SRC2,
      "D[i][j] = Jni[i][0] * Jo[0][j] + Jni[i][1] * Jo[1][j];",
      "D[i][j] = Jo[i][0] * Jni[0][j] + Jo[i][1] * Jni[1][j];",

@@ -217,3 +217,40 @@ def test_annulus_chart_derivatives():
                 Jm = (h(*(X[k] + d[k] - dj[k] for k in range(3))) - h(*(X[k] - d[k] - dj[k] for k in range(3))))
                 second = (Jp - Jm) / (4 * e * e)
                 assert np.abs(ch.hess[a * 9 + i * 3 + j] - second[a]).max() < 1e-5
+
+
+@pytest.mark.parametrize("chart", list(_charts()))
+def test_forcing_C_parallel_field_has_no_theta_part(chart):
+    """A uniform Cartesian flow V is a parallel field of flat space, so its
+    covariant derivative vanishes in every chart: with j^i = (J^-1)^i_a V^a,
+    d_k j^i = -(J^-1)^i_b d_k J^b_m j^m cancels Gamma^i_kl j^l exactly
+    (App. A).  The theta part of C^ij (Eq. forcing-C) is built from nabla_k j^i
+    alone, so C does not depend on theta for such a field.  Dropping the
+    Gamma^i_kl rho u^l term, or transposing its indices, leaves the partial
+    derivative in its place and C then moves with theta."""
+    n, N = chart.n, chart.N
+    sg, gi, gam = oracle.geometry(n, chart.g6, chart.dg18)
+    J = np.moveaxis(chart.J9.reshape(3, 3, N), 2, 0)   # [n, a, i]
+    Jinv = np.linalg.inv(J)                             # [n, i, a]
+    dJ = np.moveaxis(chart.hess.reshape(3, 3, 3, N), 3, 0)  # [n, b, m, k] = d_k J^b_m
+    rng = np.random.default_rng(21)
+    worst, scale = 0.0, 0.0
+    for v in rng.choice(N, size=12, replace=False):
+        V = 0.05 * rng.standard_normal(3)
+        rho = 1.0 + 0.05 * rng.standard_normal()
+        j = rho * Jinv[v] @ V
+        Dj = -np.einsum("ib,bmk,m->ki", Jinv[v], dJ[v], j)  # [k, i] = d_k j^i
+        T = rng.standard_normal((3, 3))
+        T = T + T.T
+        C = []
+        for theta in (CS2, 0.25):
+            _, _, c9 = oracle.forcing_moments(j, T.ravel(), Dj.ravel(), gi[:, v], gam[:, v], theta)
+            C.append(c9)
+        worst = max(worst, np.abs(C[0] - C[1]).max())
+        # what the theta part amounts to when the Christoffel term is left out
+        C0 = [oracle.forcing_moments(j, T.ravel(), Dj.ravel(), gi[:, v], np.zeros(27), th)[2]
+              for th in (CS2, 0.25)]
+        scale = max(scale, np.abs(C0[0] - C0[1]).max())
+    assert worst < 1e-15 + 1e-12 * scale, (worst, scale)
+    if np.abs(gam).max() > 1e-3:
+        assert scale > 1e-5  # the pin has teeth on this chart

@@ -23,6 +23,7 @@ from paper_1803_07822_gb300 import inputs as I
 HERE = os.path.dirname(os.path.abspath(__file__))
 BOUNDS = json.load(open(os.path.join(HERE, "golden", "paper_bounds.json")))
 P, W = oracle.PERIODIC, oracle.WALL
+CS2_ = 1.0 / 3.0
 
 
 def textbook_bgk(f0, n, tau, fext, steps):
@@ -257,3 +258,61 @@ def test_curved_rest_spurious_velocity_small_and_shrinking():
         peaks.append(np.abs(u).max())
     assert peaks[0] < 1e-3
     assert peaks[1] < peaks[0] / 1.6, peaks
+
+
+@pytest.mark.parametrize("kind", ["stretch", "shear"])
+def test_transform_literal_mode_under_stretch_and_shear(kind):
+    """Literal-a2 reading of the transformation (Sec. IV.B): a_(2) = Pi -
+    c_s^2 rho delta itself is mapped as a rank-2 tensor and f~ recomposed from
+    (rho, D a_(1), D a_(2) D^T), so the new second moment is
+    D (Pi - c_s^2 rho delta) D^T + c_s^2 rho delta; the forcing history follows
+    the same rule with b2 = C - c_s^2 A delta.  Under a stretch or a shear
+    D D^T != I, so this differs from the Pi-tensor reading (D Pi D^T), which
+    the rotation pin cannot tell apart.  The new chart is h~ = M^-1 h, so
+    D phi = J~^-1 J = J^-1 M J at every node."""
+    n = (5, 4, 6)
+    N = int(np.prod(n))
+    M = np.diag([1.12, 0.91, 1.05]) if kind == "stretch" else np.array([[1.0, 0.25, 0.0], [0.0, 1.0, 0.0],
+                                                                       [0.1, 0.0, 1.0]])
+    Mi = np.linalg.inv(M)
+    ch1 = I.channel_chart(n, I.fourier_deformation(n, 2, 0.03, 51, True, kmax=1, lmax=1))
+    J1 = ch1.J9.reshape(3, 3, N)
+    J2 = np.einsum("ab,bin->ain", Mi, J1)
+    H2 = np.einsum("ab,bjkn->ajkn", Mi, ch1.hess.reshape(3, 3, 3, N))
+    ch2 = I.Chart(n, J2.reshape(9, N), H2.reshape(27, N))
+    c, _ = oracle.lattice()
+    out = {}
+    for literal in (False, True):
+        L = oracle.Lattice(n, (P, P, P), tau=0.7, fext=(0, 2e-4, 1e-4), literal_a2=literal)
+        L.set_metric(ch1.g6, ch1.dg18)
+        L.init(1 + 0.02 * np.cos(np.arange(N)),
+               0.04 * np.sin(np.arange(3 * N).reshape(3, N)))
+        L.step(4)  # a non-equilibrium state with a non-zero history
+        sg1 = L.sqrtg.copy()
+        a0 = (L.f * sg1).sum(0)
+        a1 = np.einsum("ln,li->in", L.f * sg1, c)
+        Pi = np.einsum("ln,li,lj->ijn", L.f * sg1, c, c)
+        A = (L.Fprev * sg1).sum(0)
+        B = np.einsum("ln,li->in", L.Fprev * sg1, c)
+        C = np.einsum("ln,li,lj->ijn", L.Fprev * sg1, c, c)
+        L.transform(ch2.g6, ch2.dg18, ch1.J9, ch2.J9)
+        sg2 = L.sqrtg
+        D = np.moveaxis(np.linalg.solve(np.moveaxis(J2, 2, 0), np.moveaxis(J1, 2, 0)), 0, 2)
+        dlt = np.eye(3)[:, :, None]
+        Pi2 = np.einsum("ln,li,lj->ijn", L.f * sg2, c, c)
+        C2 = np.einsum("ln,li,lj->ijn", L.Fprev * sg2, c, c)
+        assert np.abs((L.f * sg2).sum(0) - a0).max() < 1e-14
+        assert np.abs(np.einsum("ln,li->in", L.f * sg2, c) - np.einsum("ijn,jn->in", D, a1)).max() < 1e-14
+        assert np.abs((L.Fprev * sg2).sum(0) - A).max() < 1e-15
+        assert np.abs(np.einsum("ln,li->in", L.Fprev * sg2, c) - np.einsum("ijn,jn->in", D, B)).max() < 1e-15
+        if literal:
+            ref = np.einsum("ikn,jln,kln->ijn", D, D, Pi - CS2_ * a0 * dlt) + CS2_ * a0 * dlt
+            refC = np.einsum("ikn,jln,kln->ijn", D, D, C - CS2_ * A * dlt) + CS2_ * A * dlt
+        else:
+            ref = np.einsum("ikn,jln,kln->ijn", D, D, Pi)
+            refC = np.einsum("ikn,jln,kln->ijn", D, D, C)
+        assert np.abs(Pi2 - ref).max() < 1e-14
+        assert np.abs(C2 - refC).max() < 1e-15 + 1e-12 * np.abs(refC).max()
+        out[literal] = Pi2
+    # the two readings differ here by c_s^2 rho (delta - D D^T)
+    assert np.abs(out[True] - out[False]).max() > 1e-3
