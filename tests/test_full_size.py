@@ -1,5 +1,6 @@
 """The benchmark's workloads at their full sizes, in the launch configuration
-bench.py times, against the oracle: over the whole field, one cycle of the
+bench.py times, against the oracle: over the whole field (and over each
+non-periodic face plane and the interior on its own), one cycle of the
 128 x 128 x 256 dynamic channel (chart change with transformation, face
 velocities, 10 steps through the default step pass, mass and wall force) and
 5 steps of the 4096 x 1024 D2Q9 channel.  The 256^3 channel and the full
@@ -12,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1803_07822_gb300 import inputs as I
+from planes import assert_regions
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,6 +59,8 @@ def test_dynamic_channel_one_bench_cycle():
     ro, uo = o.moments(ch1.J9)
     print(f"\n128x128x256 dynamic channel, one cycle: rel L2 rho {rel(rg, ro):.2e}, u {rel(ug, uo):.2e}")
     assert rel(rg, ro) < 1e-5 and rel(ug, uo) < 1e-5
+    errs = assert_regions(rg, ug, ro, uo, spec["n"], w["bc_lo"], w["bc_hi"], 1e-5, "128x128x256")
+    print("  " + ", ".join(f"{k}: rho {v[0]:.1e} u {v[1]:.1e}" for k, v in errs.items()))
     assert abs(g.total_mass() - o.mass()) < 1e-6 * o.mass()
     Fg, Fo = g.wall_force(2, 1), o.wall_force(2, 1, ch1.J9)
     assert np.abs(Fg - Fo).max() < 1e-5 * np.abs(Fo).max()

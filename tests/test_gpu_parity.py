@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Same seeded inputs on both sides; element-by-element comparison of density
-and velocity (relative L2 over all nodes), mass and wall force.  Bars:
+and velocity (relative L2 over all nodes, and over each non-periodic face
+plane and the interior on its own), mass and wall force.  Bars:
 FP64 storage 1e-11, FP32 storage 1e-5 (the method's FP32 target after 1000
 steps), FP16/BF16 weight-shifted storage a stated bound.  Sizes are odd and
 ragged on purpose (not multiples of the kernels' tiles).
@@ -11,6 +12,7 @@ import pytest
 
 import oracle
 from paper_1803_07822_gb300 import inputs as I
+from planes import assert_regions
 
 pytestmark = pytest.mark.gpu
 
@@ -37,11 +39,14 @@ def make_pair(w, storage, literal=False, step_kernel="auto"):
 
 
 def compare(g, o, J9, tol, tag=""):
+    """All-node relative L2 of rho and of the Cartesian velocity, and the same
+    over each non-periodic face plane and the interior, each under tol."""
     rg, ug = g.moments(cartesian=True)
     ro, uo = o.moments(J9)
     er, eu = rel(rg, ro), rel(ug, uo)
     assert np.isfinite(ug).all()
     assert er < tol and eu < tol, f"{tag} rho {er:.3e} u {eu:.3e} (tol {tol})"
+    assert_regions(rg, ug, ro, uo, o.n, tuple(o.params.bc_lo), tuple(o.params.bc_hi), tol, tag)
     return er, eu
 
 
