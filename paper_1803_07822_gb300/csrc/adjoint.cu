@@ -28,6 +28,7 @@
 #include <string>
 
 #include "ctx.h"
+#include "make_lat.h"
 #include "adjoint.cuh"
 
 namespace cslbm {
@@ -489,23 +490,6 @@ __global__ void __launch_bounds__(128) k_adj_metric(long long N, const double* _
         for (int k = 0; k < 6; k++) ldg18[(a * 6 + k) * N + v] = ldg[a][k];
 }
 
-inline Lat lat_of(const cslbm_ctx* c)
-{
-    Lat L;
-    for (int a = 0; a < 3; a++) {
-        L.n[a] = c->n[a];
-        L.bclo[a] = c->p.bc_lo[a];
-        L.bchi[a] = c->p.bc_hi[a];
-        L.fext[a] = c->p.fext[a];
-    }
-    L.N = c->N;
-    L.omega = 1.0 / c->p.tau;
-    L.kvisc = 1.0 - 0.5 / c->p.tau;
-    L.theta = c->theta;
-    for (int k = 0; k < 6; k++) L.face[k] = c->face[k];
-    return L;
-}
-
 template <class R> Bufs<R> bufs(const cslbm_ctx* c)
 {
     const size_t N = c->N;
@@ -549,7 +533,7 @@ template <class R> void finish_step(cslbm_ctx* c, const Lat& L, Bufs<R>& B, int 
 
 template <class R> void seed(cslbm_ctx* c, int axis, int side, const double e[3])
 {
-    Lat L = lat_of(c);
+    Lat L = make_lat(c);
     Bufs<R> B = bufs<R>(c);
     const int lp = c->adj.lp;
     const size_t N = c->N;
@@ -567,7 +551,7 @@ template <class R> void seed(cslbm_ctx* c, int axis, int side, const double e[3]
 
 template <class R> void backward(cslbm_ctx* c)
 {
-    Lat L = lat_of(c);
+    Lat L = make_lat(c);
     Bufs<R> B = bufs<R>(c);
     const int lp = c->adj.lp, dst = 1 - lp;
     c->ops->momentum_field(c);  // rho u at time t
@@ -584,7 +568,7 @@ template <class R> void backward(cslbm_ctx* c)
 
 template <class R> void init_back(cslbm_ctx* c)
 {
-    Lat L = lat_of(c);
+    Lat L = make_lat(c);
     Bufs<R> B = bufs<R>(c);
     const int lp = c->adj.lp;
     k_adj_init<R><<<nb(c->N, 256), 256, 0, c->stream>>>(L, (const R*)c->G[c->gc], B.lP[lp], B.lH[lp], B.lGeo);

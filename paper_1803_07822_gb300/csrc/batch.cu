@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "make_lat.h"
 #include "flat_step.cuh"
 
 namespace cslbm {
@@ -125,23 +126,6 @@ cslbm_status bfail(cslbm_status s, const std::string& m) { return cslbm_record_e
         if (e_ != cudaSuccess) return bfail(CSLBM_ECUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-cslbm::Lat lat_of(const cslbm_ctx* c)
-{
-    cslbm::Lat L;
-    for (int a = 0; a < 3; a++) {
-        L.n[a] = c->n[a];
-        L.bclo[a] = c->p.bc_lo[a];
-        L.bchi[a] = c->p.bc_hi[a];
-        L.fext[a] = c->p.fext[a];
-    }
-    L.N = c->N;
-    L.omega = 1.0 / c->p.tau;
-    L.kvisc = 1.0 - 0.5 / c->p.tau;
-    L.theta = c->theta;
-    for (int k = 0; k < 6; k++) L.face[k] = c->face[k];
-    return L;
-}
-
 bool table_current(const cslbm_batch* b)
 {
     if (!b->have_table) return false;
@@ -158,7 +142,7 @@ cslbm_status upload_table(cslbm_batch* b)
     for (int i = 0; i < b->nb; i++) {
         const cslbm_ctx* c = b->ctx[i];
         Chan& t = b->h_tab[i];
-        t.L = lat_of(c);
+        t.L = cslbm::make_lat(c);
         for (int k = 0; k < 2; k++) {
             t.P[k] = (float*)c->P[k];
             t.H[k] = (float*)c->H[k];

@@ -23,6 +23,7 @@
 
 #include "ctx.h"
 #include "lbm_device.cuh"
+#include "make_lat.h"
 
 namespace {
 
@@ -84,27 +85,10 @@ __global__ void __launch_bounds__(kBlock) k_sum_partials(double* partials, long 
     if (threadIdx.x == 0) partials[kMaxPartials] = part[0];
 }
 
-cslbm::Lat lat_of(const cslbm_ctx* c)
-{
-    cslbm::Lat L;
-    for (int a = 0; a < 3; a++) {
-        L.n[a] = c->n[a];
-        L.bclo[a] = c->p.bc_lo[a];
-        L.bchi[a] = c->p.bc_hi[a];
-        L.fext[a] = c->p.fext[a];
-    }
-    L.N = c->N;
-    L.omega = 1.0 / c->p.tau;
-    L.kvisc = 1.0 - 0.5 / c->p.tau;
-    L.theta = c->theta;
-    for (int k = 0; k < 6; k++) L.face[k] = c->face[k];
-    return L;
-}
-
 template <class S, class R>
 void launch(const cslbm_ctx* c, double* partials, unsigned nb)
 {
-    k_mass_partials<S, R><<<nb, kBlock, 0, c->stream>>>(lat_of(c), (const S*)c->P[c->pc], (const R*)c->H[c->hc],
+    k_mass_partials<S, R><<<nb, kBlock, 0, c->stream>>>(cslbm::make_lat(c), (const S*)c->P[c->pc], (const R*)c->H[c->hc],
                                                        (const R*)c->G[c->gc], partials);
 }
 
@@ -141,6 +125,7 @@ cslbm_status cslbm_total_mass_static(cslbm_ctx* c, double* out)
     default: launch<double, double>(c, partials, (unsigned)nb); break;
     }
     k_sum_partials<<<1, kBlock, 0, c->stream>>>(partials, nb);
+    c->launches += 2;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, partials + kMaxPartials, sizeof(double), cudaMemcpyDeviceToHost,
                                               c->stream);

@@ -5,7 +5,8 @@ mass (a real-time loop or host callback that must stay out of the CUDA
 allocator, a plugin whose framework owns all allocations).  Its partial sums
 live in a fixed device array instead of the context's workspace.  Checked
 through the C ABI against cslbm_total_mass on two calls in a row, on two
-lattices, so that the second call runs on the array the first one left.
+lattices, so that the second call runs on the array the first one left, and
+against the oracle's mass of the same run, in every storage format.
 This file is collected after the other files; only tests marked late run
 after it.
 """
@@ -19,6 +20,9 @@ from paper_1803_07822_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+# mass against the oracle after 25 steps, by storage of the populations
+ORACLE_TOL = {"fp64": 1e-12, "fp32": 1e-6, "fp16": 1e-4, "bf16": 1e-3}
+
 
 def mass_pair(lat):
     lib = _abi.load()
@@ -28,11 +32,12 @@ def mass_pair(lat):
     return a.value, b.value
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16", "fp64"])
 def test_static_mass_matches_workspace_mass_twice(storage):
     from paper_1803_07822_gb300.lattice import CurvedLattice
     w1 = I.plain_fp64_channel()
     w2 = I.dynamic_channel(n=(37, 41, 23), seed=7, n_modes=4, amp=0.05, tau=0.7, re=10.0, kmax=2, lmax=1)
+    import oracle
     results = []
     for w in (w1, w2):
         lat = CurvedLattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=storage)
@@ -45,6 +50,14 @@ def test_static_mass_matches_workspace_mass_twice(storage):
         again = lat.total_mass_static()
         assert got == again  # fixed summation order: the same bits on a repeat
         results.append((ref, got))
+        # and against the oracle's mass of the same run (sum of sqrt(g) rho)
+        o = oracle.Lattice(w["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"])
+        o.set_metric(w["chart"].g6, w["chart"].dg18)
+        for (a, s), u in w["faces"].items():
+            o.set_face_velocity(a, s, u)
+        o.init()
+        o.step(25)
+        assert abs(got - o.mass()) <= ORACLE_TOL[storage] * o.mass()
     for ref, got in results:
         assert abs(got - ref) <= 1e-12 * abs(ref)
     assert results[0][0] != results[1][0]
