@@ -9,27 +9,12 @@
 #include "flat_step.cuh"
 #include "fused_rows.cuh"
 #include "lbm_device.cuh"
+#include "fp_convert.h"
+#include "make_lat.h"
 
 namespace cslbm {
 
 constexpr int TPB = 256;
-
-inline Lat make_lat(const cslbm_ctx* c)
-{
-    Lat L;
-    for (int a = 0; a < 3; a++) {
-        L.n[a] = c->n[a];
-        L.bclo[a] = c->p.bc_lo[a];
-        L.bchi[a] = c->p.bc_hi[a];
-        L.fext[a] = c->p.fext[a];
-    }
-    L.N = c->N;
-    L.omega = 1.0 / c->p.tau;
-    L.kvisc = 1.0 - 0.5 / c->p.tau;
-    L.theta = c->theta;
-    for (int k = 0; k < 6; k++) L.face[k] = c->face[k];
-    return L;
-}
 
 inline unsigned nblocks(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
 
@@ -45,6 +30,11 @@ __device__ __forceinline__ void node_coords(const Lat& L, long long v, int& x, i
 // Metric update (App. A): inverse metric by cofactors in FP64, sqrt(det g),
 // then Gamma^i_jk = 1/2 g^il (d_j g_kl + d_k g_jl - d_l g_jk) in R.
 // ---------------------------------------------------------------------------
+// a double rounded to the compute type (FP32 on the integer units)
+template <class R> __device__ __forceinline__ R to_real(double x);
+template <> __device__ __forceinline__ float to_real<float>(double x) { return f64_to_f32_rn(x); }
+template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+
 template <class R>
 __global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, const double* __restrict__ dg18,
                                                 long long stride, long long v0, long long cnt, R* __restrict__ geo,
@@ -65,34 +55,39 @@ __global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, c
     // 1/det and sqrt(det) in FP64.  For FP32-and-narrower storage they start
     // from FP32 estimates refined by one Newton step each (relative error
     // ~1e-14 before the rounding to R), which spares the FP64 divide and
-    // square root; FP64 storage divides exactly.
+    // square root; FP64 storage divides exactly.  The conversions between
+    // FP64 and FP32 run on the integer units (fp_convert.h): as FP64-pipe
+    // instructions they were most of this kernel's time.
     double id, sd;
     if constexpr (std::is_same<R, double>::value) {
         id = 1.0 / det;
         sd = sqrt(det);
     } else {
-        if (det > 1e-30 && det < 1e30) {
-            const double r0 = (double)__frcp_rn((float)det);
-            id = fma(r0, fma(-det, r0, 1.0), r0);          // r0 (2 - det r0)
-            const double y0 = (double)rsqrtf((float)det);  // ~ 1/sqrt(det)
+        // 1e-30 < det < 1e30, compared on the bit patterns of positive doubles
+        const long long bits = __double_as_longlong(det);
+        if (bits > 0x39B4484BFEEBC2A0ll && bits < 0x46293E5939A08CEAll) {
+            const float df = f64_to_f32_rn(det);
+            const double r0 = f32_to_f64(__frcp_rn(df));
+            id = fma(r0, fma(-det, r0, 1.0), r0);        // r0 (2 - det r0)
+            const double y0 = f32_to_f64(rsqrtf(df));    // ~ 1/sqrt(det)
             const double s0 = det * y0;
-            sd = fma(0.5 * y0, fma(-s0, s0, det), s0);     // s0 + (det - s0^2) / (2 s0)
+            sd = fma(0.5 * y0, fma(-s0, s0, det), s0);   // s0 + (det - s0^2) / (2 s0)
         } else {
             id = 1.0 / det;
             sd = sqrt(det);
         }
     }
     double gi[6] = {A * id, B * id, C * id, (a * f - c * c) * id, (b * c - a * e) * id, (a * d - b * b) * id};
-    geo[v] = R(sd);
-#pragma unroll
-    for (int k = 0; k < 6; k++) geo[(1 + k) * N + v] = R(gi[k]);
     R dg[3][6], gr[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) gr[m] = to_real<R>(gi[m]);
+    geo[v] = to_real<R>(sd);
+#pragma unroll
+    for (int k = 0; k < 6; k++) geo[(1 + k) * N + v] = gr[k];
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-        for (int m = 0; m < 6; m++) dg[k][m] = R(dg18[(k * 6 + m) * stride + t]);
-#pragma unroll
-    for (int m = 0; m < 6; m++) gr[m] = R(gi[m]);
+        for (int m = 0; m < 6; m++) dg[k][m] = to_real<R>(dg18[(k * 6 + m) * stride + t]);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -375,8 +370,8 @@ __device__ __forceinline__ void dphi(const double (&Jn)[9], const double (&Jo)[9
     Cm n[9], o[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-        n[k] = Cm(Jn[k]);
-        o[k] = Cm(Jo[k]);
+        n[k] = to_real<Cm>(Jn[k]);
+        o[k] = to_real<Cm>(Jo[k]);
     }
     Cm inv[9];
     {
