@@ -160,13 +160,48 @@ __device__ __forceinline__ Mom4<R> mom_site(const Lat& L, const Mom4<R>* __restr
     return acc;
 }
 
+// L2 eviction policies (createpolicy): data read or written once per step
+// goes out of L2 first; data read again within the step stays longer
+__device__ __forceinline__ unsigned long long policy_evict_first()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+// a store carrying an L2 eviction policy
+__device__ __forceinline__ void st_hint(float* p, float v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;\n" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(double* p, double v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;\n" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(__half* p, float v, unsigned long long pol)
+{
+    const unsigned short b = __half_as_ushort(__float2half_rn(v));
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;\n" ::"l"(p), "h"(b), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(__nv_bfloat16* p, float v, unsigned long long pol)
+{
+    const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;\n" ::"l"(p), "h"(b), "l"(pol) : "memory");
+}
+
 // the step of one node from its populations s (h - w), geometry and history
 // at element offset v, and the rho u differences d across the nine opposite
-// stencil pairs; stores the new populations and forcing coefficients
-template <class S, class R>
+// stencil pairs; stores the new populations and forcing coefficients (with
+// the L2 policy pol when HINT)
+template <class S, class R, bool HINT = false>
 __device__ __forceinline__ void step_core(const Lat& L, const R s[Q], const GeoT<R>& G, const HistT<R>& Hp,
                                           const R d[9][3], S* __restrict__ Pout, R* __restrict__ hout, unsigned v,
-                                          unsigned N)
+                                          unsigned N, unsigned long long pol = 0)
 {
     PairSums<R> Ps;
     pair_sums(s, Ps);
@@ -186,13 +221,23 @@ __device__ __forceinline__ void step_core(const Lat& L, const R s[Q], const GeoT
     forcing_t<R, R>(R(L.theta), fext, G, j, Tt, D, H);
     R out[Q];
     collide_t<R, R>(R(L.omega), R(L.theta), G, s, m0, rho, ir, j, Hp, H, out);
-    hout[v] = H.A;
+    if constexpr (HINT) {
+        st_hint(hout + v, H.A, pol);
 #pragma unroll
-    for (int a = 0; a < 3; a++) hout[(1 + a) * N + v] = H.B[a];
+        for (int a = 0; a < 3; a++) st_hint(hout + (1 + a) * N + v, H.B[a], pol);
 #pragma unroll
-    for (int a = 0; a < 6; a++) hout[(4 + a) * N + v] = H.C[a];
+        for (int a = 0; a < 6; a++) st_hint(hout + (4 + a) * N + v, H.C[a], pol);
 #pragma unroll
-    for (int l = 0; l < Q; l++) Store<S>::st(Pout + (unsigned)pslot(l) * N + v, out[l]);
+        for (int l = 0; l < Q; l++) st_hint(Pout + (unsigned)pslot(l) * N + v, out[l], pol);
+    } else {
+        hout[v] = H.A;
+#pragma unroll
+        for (int a = 0; a < 3; a++) hout[(1 + a) * N + v] = H.B[a];
+#pragma unroll
+        for (int a = 0; a < 6; a++) hout[(4 + a) * N + v] = H.C[a];
+#pragma unroll
+        for (int l = 0; l < Q; l++) Store<S>::st(Pout + (unsigned)pslot(l) * N + v, out[l]);
+    }
 }
 
 template <class R>

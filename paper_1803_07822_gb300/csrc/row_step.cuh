@@ -33,8 +33,6 @@
 namespace cslbm {
 namespace rows {
 
-constexpr unsigned long long kWaitNs = 500000000ull;
-
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count)
@@ -65,14 +63,15 @@ __device__ __forceinline__ unsigned long long now_ns()
     asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
     return t;
 }
-// false when the phase of the given parity did not complete within kWaitNs
-__device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity)
+// false when the phase of the given parity did not complete within limit_ns
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity,
+                                         unsigned long long limit_ns = kWaitNs)
 {
     if (bar_try(b, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (;;) {
         if (bar_try(b, parity)) return true;
-        if (now_ns() - t0 > kWaitNs) return false;
+        if (now_ns() - t0 > limit_ns) return false;
     }
 }
 // global -> shared bulk copy of `bytes` (16-byte aligned, a multiple of 16)
@@ -128,6 +127,66 @@ __device__ __forceinline__ void tensor4(void* dst, const CUtensorMap* map, int c
         : "memory");
 }
 
+// the same copies carrying an L2 eviction policy (createpolicy)
+__device__ __forceinline__ void tensor2(void* dst, const CUtensorMap* map, int c0, int c1, unsigned long long* b,
+                                        unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3}], [%4], %5;\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(su32(b)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void tensor3(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                        unsigned long long* b, unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3, %4}], [%5], %6;\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(su32(b)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void tensor4(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                        unsigned long long* b, unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6], %7;\n" ::"r"(su32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(b)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* b,
+                                          unsigned long long pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;\n" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(b)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ unsigned long long policy_evict_unchanged()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_unchanged.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
+// L2 policies of the staged copies: `once` for data whose last read in the
+// step this is (populations in the step stage, geometry, history), `keep`
+// for data read again later in the step (the momentum stage's populations,
+// sqrt(g), A and B), `shared` for rho u, read by the nine tiles around a row
+struct Pol {
+    unsigned long long once, keep, shared;
+};
+__device__ __forceinline__ Pol make_pol()
+{
+    Pol p;
+    p.once = policy_evict_first();
+    p.keep = policy_evict_last();
+    p.shared = policy_evict_unchanged();
+    return p;
+}
+
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -162,7 +221,8 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
                                            const CUtensorMap* mhist,
                                            int t, unsigned char* st,
                                            unsigned long long* bar, const S* __restrict__ Pin,
-                                           const Mom4<float>* __restrict__ jf, int lane, int part, int stride = 32)
+                                           const Mom4<float>* __restrict__ jf, int lane, int part, const Pol& pol,
+                                           int stride = 32)
 {
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
     const unsigned N = (unsigned)L.N;
@@ -186,7 +246,8 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
             bool in = true;
             const int zs = wrap_or(z - cvec_rt(d, 2), n2, zper, in);
             bar_expect_tx(bar, (unsigned)(cnt * pl.TR * n0 * sizeof(S)));
-            tensor4(st + (size_t)base * NT * sizeof(S), cnt == 3 ? mpop3 : mpop, 0, y0 - cvec_rt(d, 1), zs, base, bar);
+            tensor4(st + (size_t)base * NT * sizeof(S), cnt == 3 ? mpop3 : mpop, 0, y0 - cvec_rt(d, 1), zs, base, bar,
+                    pol.once);
             continue;
         }
         if (c < npop) {
@@ -196,7 +257,7 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
             if (!seam) {
                 const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
                 bar_expect_tx(bar, bytes);
-                tensor4(st + (size_t)q * NT * sizeof(S), mpop, 0, y0 - cvec_rt(l, 1), zs, q, bar);
+                tensor4(st + (size_t)q * NT * sizeof(S), mpop, 0, y0 - cvec_rt(l, 1), zs, q, bar, pol.once);
                 continue;
             }
             const int y = y0 + r;
@@ -205,12 +266,12 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
             const unsigned bytes = (unsigned)(n0 * sizeof(S));
             bar_expect_tx(bar, bytes);
             bulk_copy(st + (size_t)(q * NT + r * n0) * sizeof(S), Pin + (size_t)q * N + ((unsigned)zs * n1 + ys) * n0,
-                      bytes, bar);
+                      bytes, bar, pol.once);
         } else if (c < npop + njf && jf_one) {
             // rows y0 - 1 .. y0 + TR of planes z - 1 .. z + 1 (row -1 of the first
             // tile is the fill: only face rows use it)
             bar_expect_tx(bar, (unsigned)(3 * (pl.TR + 2) * n0 * sizeof(Mom4<float>)));
-            tensor3(st + pl.off_jf, mjf3, 0, (y0 - 1) * 4 * n0 / pl.JL, z - 1, bar);
+            tensor3(st + pl.off_jf, mjf3, 0, (y0 - 1) * 4 * n0 / pl.JL, z - 1, bar, pol.shared);
         } else if (c < npop + njf) {
             const int k = c - npop, a = seam ? k / (TRe + 2) : k, b = seam ? k - a * (TRe + 2) : 0;
             bool in = true;
@@ -224,20 +285,20 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
                 // the first tile reads the previous plane's last row or the
                 // fill: only face rows use it)
                 const int line = (int)(((long long)zs * n1 + y0 - 1) * 4 * n0 / pl.JL);
-                tensor2(dst, mjf, 0, line, bar);
+                tensor2(dst, mjf, 0, line, bar, pol.shared);
                 continue;
             }
             const int ys = wrap_or(y0 - 1 + b, n1, yper, in);
             if (!in) continue;
             const unsigned bytes = (unsigned)(n0 * sizeof(Mom4<float>));
             bar_expect_tx(bar, bytes);
-            bulk_copy(dst, jf + ((unsigned)zs * n1 + ys) * n0, bytes, bar);
+            bulk_copy(dst, jf + ((unsigned)zs * n1 + ys) * n0, bytes, bar, pol.shared);
         } else if (c == npop + njf) {
             bar_expect_tx(bar, NGEO * NT * 4u);
-            tensor2(st + pl.off_geo, mgeo, (int)v0, 0, bar);
+            tensor2(st + pl.off_geo, mgeo, (int)v0, 0, bar, pol.once);
         } else {
             bar_expect_tx(bar, NHIST * NT * 4u);
-            tensor2(st + pl.off_hist, mhist, (int)v0, 0, bar);
+            tensor2(st + pl.off_hist, mhist, (int)v0, 0, bar, pol.once);
         }
     }
 }
@@ -248,7 +309,8 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
 // Nodes on a face are left to k_step_faces.
 template <class S>
 __device__ __forceinline__ void step_tile(const Lat& L, const Plan& pl, const unsigned char* st, int t, int tid,
-                                          unsigned long long* empty, S* __restrict__ Pout, float* __restrict__ hout)
+                                          unsigned long long* empty, S* __restrict__ Pout, float* __restrict__ hout,
+                                          unsigned long long pol_store)
 {
     const int n0 = L.n[0], n1 = L.n[1];
     const unsigned N = (unsigned)L.N;
@@ -308,7 +370,7 @@ __device__ __forceinline__ void step_tile(const Lat& L, const Plan& pl, const un
         for (int k = 0; k < 3; k++)
             G.gc[k] = (G.gam[0 * 6 + s6(k, 0)] + G.gam[1 * 6 + s6(k, 1)]) + G.gam[2 * 6 + s6(k, 2)];
         const unsigned v = ((unsigned)z * n1 + y) * n0 + x;
-        step_core<S, float>(L, sv, G, Hp, d, Pout, hout, v, N);
+        step_core<S, float, true>(L, sv, G, Hp, d, Pout, hout, v, N, pol_store);
     }
 }
 
@@ -335,6 +397,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     if (tid >= NT) {
         // copy warp
         const int lane = tid - NT;
+        const Pol pol = make_pol();
         int i = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < pl.ntiles; t += gridDim.x, i++) {
@@ -345,8 +408,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
             issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.jf3, &M.geo, &M.hist, t, smem_rows + (size_t)s * pl.stage_bytes,
-                          &full[s],
-                          Pin, jf, lane, PART_MAIN | PART_JF);
+                          &full[s], Pin, jf, lane, PART_MAIN | PART_JF, pol);
             __syncwarp();
             if (lane == 0) bar_arrive(&full[s]);
         }
@@ -356,6 +418,7 @@ __global__ void __launch_bounds__(NTHR, 1)
             if (!bar_wait(&full[j % STAGES], (j / STAGES) & 1) && lane == 0) atomicOr(err, 2);
     } else {
         // compute warps
+        const unsigned long long pol_store = policy_evict_first();
         int i = 0;
         for (int t = blockIdx.x; t < pl.ntiles; t += gridDim.x, i++) {
             const int s = i % STAGES;
@@ -363,7 +426,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                 atomicOr(err, 4);
                 break;
             }
-            step_tile<S>(L, pl, smem_rows + (size_t)s * pl.stage_bytes, t, tid, &empty[s], Pout, hout);
+            step_tile<S>(L, pl, smem_rows + (size_t)s * pl.stage_bytes, t, tid, &empty[s], Pout, hout, pol_store);
         }
     }
     __syncthreads();
