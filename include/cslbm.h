@@ -44,7 +44,7 @@ typedef enum {
     CSLBM_ECUDA = 2,     /* a CUDA call failed; the message names it */
     CSLBM_ENOMEM = 3,    /* workspace smaller than cslbm_workspace_bytes */
     CSLBM_EUNSTABLE = 4, /* non-finite density or velocity found by cslbm_check */
-    CSLBM_ETIMEOUT = 5,  /* reserved: a bounded device wait expired */
+    CSLBM_ETIMEOUT = 5,  /* a bounded device wait of the fused step pass expired */
     CSLBM_ESTATE = 6     /* call out of order (e.g. step before init) */
 } cslbm_status;
 
@@ -167,6 +167,20 @@ cslbm_status cslbm_wall_force(cslbm_ctx* ctx, int axis, int side, double out3[3]
  * wait of the row-staged or fused step pass that ran out (ETIMEOUT; the
  * pass's counters are reset).  ESTATE before cslbm_init_equilibrium. Syncs. */
 cslbm_status cslbm_check(cslbm_ctx* ctx);
+
+/* Test hook of the bounded waits (no counterpart in the paper).  The fused
+ * step pass synchronises its CTAs through per-iteration publication counts,
+ * and every wait in it gives up after half a second, setting the error flag
+ * that cslbm_check reports as CSLBM_ETIMEOUT.  This call makes the next
+ * fused launch of ctx (one cslbm_step LBM step; later launches are
+ * unaffected) give up after wait_ns nanoseconds instead, and makes its CTA 0
+ * leave momentum iteration `iteration` uncounted, so that every step tile
+ * waiting on that iteration times out.  The state that step leaves is not a
+ * valid LBM state (tiles stepped without their rho u rows); restore one with
+ * cslbm_load_state after cslbm_check.  EINVAL when the fused pass does not
+ * apply to ctx (see cslbm_params.step_kernel), for iteration < 0, or for
+ * wait_ns outside (0, 5e8]. */
+cslbm_status cslbm_test_withhold_publication(cslbm_ctx* ctx, int iteration, long long wait_ns);
 
 /* Checkpoint: the bytes of the evolving state (distributions + forcing
  * history), copied to/from `buf` (device or host per on_device).  EINVAL for a

@@ -58,6 +58,7 @@ SIGNATURES = {
     "cslbm_total_mass": [_P, _D],
     "cslbm_total_mass_static": [_P, _D],
     "cslbm_wall_force": [_P, _I, _I, _D],
+    "cslbm_test_withhold_publication": [_P, _I, ctypes.c_longlong],
     "cslbm_check": [_P],
     "cslbm_state_bytes": [_P, ctypes.POINTER(_SZ)],
     "cslbm_save_state": [_P, _P, _SZ, _I],

@@ -205,6 +205,8 @@ void rows_prepare(cslbm_ctx* c)
     R.ok = 0;
     R.fused_ok = 0;
     R.epoch = 0;
+    R.test_wait_ns = 0;
+    R.test_withhold = -1;
     if (c->p.step_kernel == CSLBM_STEP_FLAT || c->p.storage == CSLBM_FP64) return;
     int max_smem = 0;
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return;
@@ -580,6 +582,18 @@ cslbm_status cslbm_check(cslbm_ctx* c)
         snprintf(m, sizeof m, "%.0f nodes with non-finite density or |v| > 0.3", bad);
         return fail(CSLBM_EUNSTABLE, m);
     }
+    return CSLBM_OK;
+}
+
+cslbm_status cslbm_test_withhold_publication(cslbm_ctx* c, int iteration, long long wait_ns)
+{
+    if (!c) return fail(CSLBM_EINVAL, "ctx is null");
+    if (!c->rows.fused_ok || c->p.step_kernel != CSLBM_STEP_AUTO)
+        return fail(CSLBM_EINVAL, "the fused step pass does not apply to this lattice");
+    if (iteration < 0 || wait_ns <= 0 || wait_ns > (long long)cslbm::rows::kWaitNs)
+        return fail(CSLBM_EINVAL, "iteration must be >= 0 and wait_ns in (0, 5e8]");
+    c->rows.test_withhold = iteration;
+    c->rows.test_wait_ns = (unsigned long long)wait_ns;
     return CSLBM_OK;
 }
 

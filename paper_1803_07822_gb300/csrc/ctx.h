@@ -30,6 +30,8 @@ struct cslbm_rows {
     CUtensorMap hist4[2]; // A and B of the history, box NT x 4
     unsigned* done;       // [iterations] CTAs that published each momentum iteration (cumulative)
     unsigned epoch;       // fused launches so far
+    unsigned long long test_wait_ns;  // next fused launch only: wait limit (0: the default)
+    int test_withhold;    // next fused launch only: iteration CTA 0 does not count as published (-1: none)
     unsigned off_m, off_sg, off_h4, off_js, fused_bytes;
 };
 

@@ -30,7 +30,10 @@
 // otherwise.
 //
 // All CTAs must be resident at once (cooperative launch); every wait is
-// bounded and reports through *err.
+// bounded (half a second, or the limit of the test hook) and reports through
+// *err: bit 1 a copy that did not land, 2 a stage wait of the compute warps,
+// 8 a copy warp that stopped early, 16 a step tile whose rho u rows were not
+// published in time, 32 / 64 the shared rho u tile's hand-over.
 #pragma once
 
 #include "row_step.cuh"
@@ -112,7 +115,7 @@ static __device__ __noinline__ bool face_momentum(const Lat& L, int xi, int yi, 
 template <class S>
 __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FMaps& M, int t, unsigned char* st,
                                           unsigned long long* bar, const S* __restrict__ Pin, int lane,
-                                          unsigned off_sg, unsigned off_h4)
+                                          unsigned off_sg, unsigned off_h4, unsigned long long keep)
 {
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
     const unsigned N = (unsigned)L.N;
@@ -130,7 +133,7 @@ __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FM
             const int zs = wrap_or(z - cvec_rt(d, 2), n2, zper, in);
             bar_expect_tx(bar, (unsigned)(cnt * pl.TR * n0 * sizeof(S)));
             tensor4(st + (size_t)base * NT * sizeof(S), cnt == 3 ? &M.pop3 : &M.pop, 0, y0 - cvec_rt(d, 1), zs, base,
-                    bar);
+                    bar, keep);
             continue;
         }
         if (c < npop) {
@@ -140,7 +143,7 @@ __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FM
             if (!seam) {
                 const unsigned bytes = (unsigned)(pl.TR * n0 * sizeof(S));
                 bar_expect_tx(bar, bytes);
-                tensor4(st + (size_t)q * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, q, bar);
+                tensor4(st + (size_t)q * NT * sizeof(S), &M.pop, 0, y0 - cvec_rt(l, 1), zs, q, bar, keep);
                 continue;
             }
             const int ys = wrap_or(y0 + r - cvec_rt(l, 1), n1, yper, in);
@@ -148,13 +151,13 @@ __device__ __forceinline__ void issue_mom(const Lat& L, const Plan& pl, const FM
             const unsigned bytes = (unsigned)(n0 * sizeof(S));
             bar_expect_tx(bar, bytes);
             bulk_copy(st + (size_t)(q * NT + r * n0) * sizeof(S), Pin + (size_t)q * N + ((unsigned)zs * n1 + ys) * n0,
-                      bytes, bar);
+                      bytes, bar, keep);
         } else if (c == npop) {
             bar_expect_tx(bar, NT * 4u);
-            tensor2(st + off_sg, &M.geo1, (int)v0, 0, bar);
+            tensor2(st + off_sg, &M.geo1, (int)v0, 0, bar, keep);
         } else {
             bar_expect_tx(bar, 4u * NT * 4u);
-            tensor2(st + off_h4, &M.hist4, (int)v0, 0, bar);
+            tensor2(st + off_h4, &M.hist4, (int)v0, 0, bar, keep);
         }
     }
 }
@@ -166,7 +169,7 @@ template <class S>
 __device__ __forceinline__ void mom_tile(const Lat& L, const Plan& pl, const unsigned char* st, int t, int tid,
                                          unsigned long long* empty, unsigned long long* jfree, unsigned jfree_parity,
                                          bool jwait, unsigned off_sg, unsigned off_h4, Mom4<float>* __restrict__ js,
-                                         Mom4<float>* __restrict__ jf, int* err)
+                                         Mom4<float>* __restrict__ jf, int* err, unsigned long long wait_ns)
 {
     const int n0 = L.n[0], n1 = L.n[1];
     const int r = tid / n0, x = tid - r * n0;
@@ -195,7 +198,7 @@ __device__ __forceinline__ void mom_tile(const Lat& L, const Plan& pl, const uns
     __syncwarp();
     if ((tid & 31) == 0) bar_arrive(empty);
     // the shared rho u tile of two iterations ago must have been read out
-    if (jwait && !bar_wait(jfree, jfree_parity)) atomicOr(err, 32);
+    if (jwait && !bar_wait(jfree, jfree_parity, wait_ns)) atomicOr(err, 32);
     bool global = false;
     if (active) {
         PairSums<float> Ps;
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
     k_step_fused(const __grid_constant__ Lat L, const __grid_constant__ Plan pl, const __grid_constant__ FMaps M,
                  const S* __restrict__ Pin, S* __restrict__ Pout, float* __restrict__ hout,
                  Mom4<float>* __restrict__ jf, unsigned* __restrict__ done, unsigned epoch, int m, unsigned off_m,
-                 unsigned off_sg, unsigned off_h4, unsigned off_js, int* err)
+                 unsigned off_sg, unsigned off_h4, unsigned off_js, int* err, unsigned long long wait_ns, int withhold)
 {
     extern __shared__ __align__(128) unsigned char smem_fused[];
     unsigned long long* fullS = reinterpret_cast<unsigned long long*>(smem_fused + off_js + 2u * NT * 16u);
@@ -301,20 +304,22 @@ __global__ void __launch_bounds__(NTHR_F, 1)
 
     if (warp == NW) {
         // momentum copy warp
+        const unsigned long long keep = policy_evict_last();
         int it = 0;
         for (; it < K; it++) {
             if (it >= 1) {
-                if (!__all_sync(0xffffffffu, bar_wait(emptyM, (it - 1) & 1))) break;
+                if (!__all_sync(0xffffffffu, bar_wait(emptyM, (it - 1) & 1, wait_ns))) break;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            issue_mom<S>(L, pl, M, b + it * G, stM, fullM, Pin, lane, off_sg, off_h4);
+            issue_mom<S>(L, pl, M, b + it * G, stM, fullM, Pin, lane, off_sg, off_h4, keep);
             __syncwarp();
             if (lane == 0) bar_arrive(fullM);
         }
         if (it < K && lane == 0) atomicOr(err, 8);
-        if (it > 0 && !bar_wait(fullM, (it - 1) & 1) && lane == 0) atomicOr(err, 2);
+        if (it > 0 && !bar_wait(fullM, (it - 1) & 1, wait_ns) && lane == 0) atomicOr(err, 2);
     } else if (warp == NW + 1) {
         // step copy warp
+        const Pol pol = make_pol();
         const unsigned target = epoch * (unsigned)G;
         unsigned pre = 0;  // cnt of the next tile's dependency, loaded ahead
         int ks = 0;
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
         for (; ks < K; ks++) {
             const int s = ks & 1, t = b + ks * G;
             if (ks >= 2) {
-                if (!__all_sync(0xffffffffu, bar_wait(&emptyS[s], ((ks >> 1) - 1) & 1))) break;
+                if (!__all_sync(0xffffffffu, bar_wait(&emptyS[s], ((ks >> 1) - 1) & 1, wait_ns))) break;
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
             unsigned char* st = smem_fused + (size_t)s * pl.stage_bytes;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                     const unsigned* c = done + dep_iteration(L, pl, t, G);
                     const unsigned long long t0 = now_ns();
                     while (!reached(ld_acquire(c), target))
-                        if (now_ns() - t0 > kWaitNs) {
+                        if (now_ns() - t0 > wait_ns) {
                             dep = 0;
                             break;
                         }
@@ -344,28 +349,31 @@ __global__ void __launch_bounds__(NTHR_F, 1)
             }
             dep = __shfl_sync(0xffffffffu, dep, 0);
             issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.jf3, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
-                          dep ? (PART_MAIN | PART_JF) : PART_MAIN);
+                          dep ? (PART_MAIN | PART_JF) : PART_MAIN, pol);
             if (lane == 0 && ks + 1 < K) pre = ld_acquire(done + dep_iteration(L, pl, t + G, G));
             __syncwarp();
             if (lane == 0) bar_arrive(&fullS[s]);
             if (!dep) {
+                // the tile went out without its rho u rows: report, stop issuing
+                if (lane == 0) atomicOr(err, 16);
                 ks++;
                 break;
             }
         }
         if (ks < K && lane == 0) atomicOr(err, 8);
         for (int j = max(0, ks - 2); j < ks; j++)
-            if (!bar_wait(&fullS[j & 1], (j >> 1) & 1) && lane == 0) atomicOr(err, 2);
+            if (!bar_wait(&fullS[j & 1], (j >> 1) & 1, wait_ns) && lane == 0) atomicOr(err, 2);
     } else if (warp == NW + 2) {
         // publishing warp: each momentum tile's rows (face rows excepted)
         // from shared memory to HBM, then the count of its iteration; a CTA
         // past its last tile counts the remaining iterations
         const bool yper = L.bclo[1] == BC_PERIODIC;
         const int Kmax = (pl.ntiles + G - 1) / G;
+        const unsigned long long keep = policy_evict_last();
         int it = 0;
         for (; it < K; it++) {
             const int bb = it & 1, t = b + it * G;
-            if (!bar_wait(&momDone[bb], (it >> 1) & 1)) {
+            if (!bar_wait(&momDone[bb], (it >> 1) & 1, wait_ns)) {
                 if (lane == 0) atomicOr(err, 64);
                 break;
             }
@@ -376,9 +384,9 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 const int yhi = (!yper && y0 + TRe - 1 == n1 - 1) ? n1 - 2 : y0 + TRe - 1;
                 if (ylo <= yhi) {
                     const unsigned bytes = (unsigned)((yhi - ylo + 1) * n0 * sizeof(Mom4<float>));
-                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;\n" ::"l"(
                                      jf + ((unsigned)z * n1 + ylo) * n0),
-                                 "r"(su32(js + bb * NT + (ylo - y0) * n0)), "r"(bytes)
+                                 "r"(su32(js + bb * NT + (ylo - y0) * n0)), "r"(bytes), "l"(keep)
                                  : "memory");
                     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
                     asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
@@ -386,34 +394,37 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 bar_arrive(&jsFree[bb]);
                 asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
                 asm volatile("fence.proxy.async.global;\n" ::: "memory");
-                red_release_add(done + it, 1u);
+                if (!(b == 0 && it == withhold)) red_release_add(done + it, 1u);
             }
             __syncwarp();
         }
         if (it == K && lane == 0)
-            for (int k = K; k < Kmax; k++) red_release_add(done + k, 1u);
+            for (int k = K; k < Kmax; k++)
+                if (!(b == 0 && k == withhold)) red_release_add(done + k, 1u);
     } else {
         // compute warps
+        const unsigned long long pol_store = policy_evict_first();
         for (int it = 0; it < K + m; it++) {
             if (it < K) {
                 const int bb = it & 1;
-                if (!bar_wait(fullM, it & 1)) {
+                if (!bar_wait(fullM, it & 1, wait_ns)) {
                     atomicOr(err, 4);
                     break;
                 }
                 mom_tile<S>(L, pl, stM, b + it * G, tid, emptyM, &jsFree[bb], ((it >> 1) - 1) & 1, it >= 2, off_sg,
-                            off_h4, js + bb * NT, jf, err);
+                            off_h4, js + bb * NT, jf, err, wait_ns);
                 __syncwarp();
                 if (lane == 0) bar_arrive(&momDone[bb]);
             }
             const int ks = it - m;
             if (ks >= 0) {
                 const int s = ks & 1;
-                if (!bar_wait(&fullS[s], (ks >> 1) & 1)) {
+                if (!bar_wait(&fullS[s], (ks >> 1) & 1, wait_ns)) {
                     atomicOr(err, 4);
                     break;
                 }
-                step_tile<S>(L, pl, smem_fused + (size_t)s * pl.stage_bytes, b + ks * G, tid, &emptyS[s], Pout, hout);
+                step_tile<S>(L, pl, smem_fused + (size_t)s * pl.stage_bytes, b + ks * G, tid, &emptyS[s], Pout, hout,
+                             pol_store);
             }
         }
     }
@@ -460,9 +471,14 @@ int launch_fused_step(cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* e
     Mom4<float>* jf = (Mom4<float>*)c->jf;
     unsigned* done = R.done;
     const rows::Plan plv = pl;
+    // the test hook of cslbm_test_withhold_publication applies to this launch only
+    unsigned long long wait_ns = R.test_wait_ns ? R.test_wait_ns : rows::kWaitNs;
+    int withhold = R.test_withhold;
+    R.test_wait_ns = 0;
+    R.test_withhold = -1;
     void* args[] = {(void*)&L, (void*)&plv, (void*)&M, (void*)&Pin, (void*)&Pout, (void*)&hout, (void*)&jf,
                     (void*)&done, (void*)&epoch, (void*)&m, (void*)&off_m, (void*)&off_sg, (void*)&off_h4,
-                    (void*)&off_js, (void*)&err};
+                    (void*)&off_js, (void*)&err, (void*)&wait_ns, (void*)&withhold};
     if (cudaLaunchCooperativeKernel((const void*)rows::k_step_fused<S>, dim3(G), dim3(rows::NTHR_F), args,
                                     R.fused_bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();

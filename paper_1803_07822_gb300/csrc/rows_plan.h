@@ -10,6 +10,8 @@ constexpr int NW = NT / 32;    // compute warps
 constexpr int NTHR = NT + 32;  // + the copy warp
 constexpr int STAGES = 2;
 constexpr int NGEO = 25, NHIST = 10;
+// limit of every wait of the row-staged and fused passes (half a second)
+constexpr unsigned long long kWaitNs = 500000000ull;
 
 // A tile is TR whole x-rows of one plane.  In a stage the populations sit at
 // [lambda][NT], rho u at [z-layer][JS] (16-byte nodes), geometry at
