@@ -1,17 +1,18 @@
 """Throughput benchmark of the curved-space LBM hot path on GB300.
 
-Workload (default): the dynamic deformed channel -- 128 x 128 x 256 nodes
-(128 span on axis 0, 256 along the flow on axis 1, 128 wall-normal on axis
-2), walls across axis 2, periodic span, parabolic inflow / outflow along the flow
-axis, tau = 0.6 (Re ~ 100), a 16-mode seeded wall deformation of 10 %
-amplitude under the time law sin^2(pi t / 2000), FP32 storage.  One bench
-step is one cycle of that schedule: metric update + transformation of f
-(every 10 LBM steps), 10 LBM steps, then the FP64 mass and wall-force
-reductions.  Metric snapshots are generated up front (the caller's job) and
-cycled.  MLUPS = lattice nodes x LBM steps / time.
+Workload (default): the 256^3 deformed channel -- 256 span on axis 0, 256
+along the flow on axis 1, 256 wall-normal on axis 2 -- walls across axis 2,
+periodic span, parabolic inflow / outflow along the flow axis, tau = 0.6
+(Re ~ 100), an 8-mode seeded wall deformation of 8 % amplitude under the
+time law sin^2(pi t / 2000), FP32 storage.  One bench step is one cycle of
+that schedule: metric update + transformation of f (every 10 LBM steps), 10
+LBM steps, then the FP64 mass and wall-force reductions.  Metric snapshots
+are generated up front (the caller's job) and cycled.  MLUPS = lattice nodes
+x LBM steps / time.  The line also carries the 128 x 128 x 256 dynamic
+channel (16 modes, 10 %) under the same schedule (`dynamic_channel`).
 
-Inputs (1.4 GB of state per LBM step) exceed the 129 MB L2, so no flush is
-needed between timed iterations.
+Inputs (5.6 GB of state per LBM step at 256^3) exceed the 129 MB L2, so no
+flush is needed between timed iterations.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -47,15 +48,13 @@ BYTES_PER_NODE = {"fp32": 19 * 4 * 2 + 10 * 4 * 2 + 25 * 4, "fp16": 19 * 2 * 2 +
                   "bf16": 19 * 2 * 2 + 80 + 100, "fp64": 19 * 8 * 2 + 80 + 100}
 # DRAM bytes per node update (dram__bytes_read.sum + dram__bytes_write.sum of
 # the kernels of one LBM step, per launch, divided by the nodes) from an ncu
-# launch list of the kernels as they stand, keyed by (pass, storage).  Empty:
-# both step passes changed after their last captures, so the line reports
-# traffic null with the older figure in a note.
+# capture of the kernels as they stand, keyed by (pass, storage, workload);
+# a workload too large for a capture takes the figure of a smaller lattice of
+# the same tile shape (the note says which).  A pass with no entry reports
+# traffic null.
 MEASURED_DRAM_BYTES_PER_NODE = {}
-TRAFFIC_NOTE = {"fused": "no capture of the current kernel; 413 B/node (fused + faces) measured before the "
-                         "three rho u layers became one copy (profiles/launches_dynamic_channel_128x128x256.md)",
-                "flat": "no capture of the current kernel; 395 B/node (both flat passes, 64x128x64 crop) measured "
-                        "before the population planes were reordered into staging groups "
-                        "(profiles/k_step_flat_crop_64x128x64.md)"}
+TRAFFIC_NOTE = {}
+NO_CAPTURE = "no ncu capture of the step kernels as they stand"
 
 
 def step_pass(n, storage, step_kernel, axis2_periodic=False):
@@ -75,14 +74,18 @@ PASS_KERNELS = {"fused": "k_step_fused + k_step_faces", "rows": "k_momentum_flat
 
 def workload_spec(name):
     if name == "dynamic":
-        return dict(n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
+        return dict(key="dynamic", n=(128, 256, 128), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0,
                     storage="fp32", label="deformed channel 128x128x256, dynamic metric (16 modes, 10 %), "
                                           "inflow/outflow, tau 0.6, Re 100, FP32, transform every 10 steps")
     if name == "crop64":
-        return dict(n=(64, 128, 64), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0, storage="fp32",
+        return dict(key="crop64", n=(64, 128, 64), seed=2000, n_modes=16, amp=0.10, tau=0.6, re=100.0, storage="fp32",
                     label="deformed channel 64x64x128 (profiling case), dynamic metric, inflow/outflow, FP32")
+    if name == "slab256":
+        return dict(key="slab256", n=(256, 256, 64), seed=3000, n_modes=8, amp=0.08, tau=0.6, re=100.0, storage="fp32",
+                    label="deformed channel 256x256x64 slab (profiling case: the 256^3 tile shape at a quarter "
+                          "of its nodes), dynamic metric (8 modes, 8 %), inflow/outflow, tau 0.6, FP32")
     if name == "target256":
-        return dict(n=(256, 256, 256), seed=3000, n_modes=8, amp=0.08, tau=0.6, re=100.0, storage="fp32",
+        return dict(key="target256", n=(256, 256, 256), seed=3000, n_modes=8, amp=0.08, tau=0.6, re=100.0, storage="fp32",
                     label="deformed channel 256^3, dynamic metric (8 modes, 8 %), inflow/outflow, tau 0.6, FP32")
     raise ValueError(name)
 
@@ -207,13 +210,13 @@ def whole_job_mlups(world, nodes_per_rank, lbm_steps, ms):
     return world * nodes_per_rank * lbm_steps / (ms * 1e-3) / 1e6
 
 
-def oracle_cycle_sample(spec, steps, warm):
+def oracle_cycle_sample(spec, steps, warm, div=2):
     """The FP64 oracle on a bounded sample of the same workload: the same
-    generator on a 1/8-volume crop (half the extent per axis), timed over
-    whole cycles (metric transform + 10 steps).  Returns (MLUPS, seconds,
-    nodes, cores)."""
+    generator on a crop of 1/div the extent per axis (1/8 of the volume by
+    default), timed over whole cycles (metric transform + 10 steps).  Returns
+    (MLUPS, seconds, nodes, cores)."""
     import oracle
-    n = tuple(v // 2 for v in spec["n"])
+    n = tuple(v // div for v in spec["n"])
     w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
                           re=spec["re"])
     snaps = snapshots(w, [500.0 + STEPS_PER_CYCLE * k for k in range(steps + warm + 1)])
@@ -723,7 +726,12 @@ def run_reference(args):
     if rank != 0:
         return
     spec = workload_spec(args.workload)
-    mlups, secs, n, cores = oracle_cycle_sample(spec, args.steps, args.warmup)
+    # the crop: half the extent per axis, or a quarter where that would take
+    # more than about 3e8 node updates (under a minute on the host cores)
+    div = 2
+    while int(np.prod([v // div for v in spec["n"]])) * STEPS_PER_CYCLE * (args.steps + args.warmup) > 3e8 and div < 8:
+        div *= 2
+    mlups, secs, n, cores = oracle_cycle_sample(spec, args.steps, args.warmup, div)
     sample = (f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, {args.steps} timed cycles "
               f"({STEPS_PER_CYCLE} steps + transform + reductions each), FP64 oracle")
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
@@ -735,51 +743,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
-    ap.add_argument("--workload", default="dynamic",
-                    choices=["dynamic", "target256", "crop64", "batch64", "adjoint64", "lgrad", "d2q9"])
-    ap.add_argument("--adjoint-steps", type=int, default=ADJOINT_STEPS,
-                    help="LBM steps of the adjoint objective (adjoint64 workload)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward step-time ratio")
-    ap.add_argument("--snapshots", type=int, default=3)
-    ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
-    ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16", "fp64"],
-                    help="storage of the populations (default: the workload's, FP32)")
-    ap.add_argument("--oracle-c1", action="store_true", help=argparse.SUPPRESS)
-    args = ap.parse_args()
-    if args.oracle_c1:  # the child process of oracle_single_thread
-        v, secs = oracle_c1_sample()
-        print(json.dumps({"value": v, "secs": secs}), flush=True)
-        return None
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batch64":
-        return bench_batch(args)
-    if args.workload in ("adjoint64", "lgrad"):
-        return bench_side(args)
-    if args.workload == "d2q9":
-        return bench_d2q9(args)
-
+def channel_cycles(spec, args, rank, world, local, steps):
+    """The channel of `spec` through `steps` timed bench cycles after
+    args.warmup, inputs resident in HBM: metric snapshots pre-generated and
+    cycled, each cycle a chart change with transformation, 10 LBM steps and
+    the mass and wall-force reductions.  Device time with CUDA events on the
+    library's stream, the slowest rank's; one LBM step timed by the library
+    (profiling on) for the roofline."""
     import torch
 
     from paper_1803_07822_gb300.lattice import CurvedLattice
-
-    rank, world, local = dist_setup(args)
-    spec = workload_spec(args.workload)
-    if args.storage:
-        spec["storage"] = args.storage
-        spec["label"] = spec["label"].replace(
-            "FP32", args.storage.upper() + (" weight-shifted storage, FP32 arithmetic" if args.storage in ("fp16", "bf16")
-                                            else " storage"))
     w = I.dynamic_channel(n=spec["n"], seed=spec["seed"] + rank, n_modes=spec["n_modes"], amp=spec["amp"],
                           tau=spec["tau"], re=spec["re"])
     N = int(np.prod(spec["n"]))
@@ -820,7 +793,7 @@ def main():
     stream = lat.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for k in range(args.steps):
+    for k in range(steps):
         cycle_dev(args.warmup + k)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -832,37 +805,104 @@ def main():
     step_ms_total, nprof, launches = lat.profile_read()
     lat.profile(False)
     ms = reduce_max(ms, world)
-    ok = lat.check()
-    ms_per_step = ms / args.steps
-    value = whole_job_mlups(world, N, STEPS_PER_CYCLE * args.steps, ms)
+    return dict(lat=lat, w=w, N=N, snaps=snaps, dev=dev, ms=ms, step_ms=step_ms_total / max(nprof, 1),
+                launches=launches, clk=clk, ok=lat.check())
 
+
+def roofline_of(spec, args, N, step_ms):
     peak, peak_kind = peaks()
-    step_ms = step_ms_total / max(nprof, 1)
     bpn = BYTES_PER_NODE[spec["storage"]]
     achieved = bpn * N / (step_ms * 1e-3) / 1e9
     sp = step_pass(spec["n"], spec["storage"], args.step_kernel)
-    mb = MEASURED_DRAM_BYTES_PER_NODE.get((sp, spec["storage"]))
-    traffic = None if mb is None else mb * N
-    e2e = None if args.no_e2e else end_to_end(args, lat, snaps, N, world)
+    mb = MEASURED_DRAM_BYTES_PER_NODE.get((sp, spec["storage"], spec["key"]))
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None if mb is None else mb * N, "peak_kind": peak_kind,
+            "kernel": "one LBM step: " + PASS_KERNELS[sp], "bytes_per_node": bpn,
+            "traffic_note": TRAFFIC_NOTE.get((sp, spec["storage"], spec["key"]), NO_CAPTURE), "step_ms": step_ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cslbm", choices=["cslbm", "reference"])
+    ap.add_argument("--workload", default="target256",
+                    choices=["target256", "dynamic", "slab256", "crop64", "batch64", "adjoint64", "lgrad", "d2q9"])
+    ap.add_argument("--adjoint-steps", type=int, default=ADJOINT_STEPS,
+                    help="LBM steps of the adjoint objective (adjoint64 workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward step-time ratio")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 128x128x256 dynamic channel reported beside the 256^3 line")
+    ap.add_argument("--snapshots", type=int, default=3)
+    ap.add_argument("--step-kernel", default="auto", choices=["auto", "rows", "flat"])
+    ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16", "fp64"],
+                    help="storage of the populations (default: the workload's, FP32)")
+    ap.add_argument("--oracle-c1", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_c1:  # the child process of oracle_single_thread
+        v, secs = oracle_c1_sample()
+        print(json.dumps({"value": v, "secs": secs}), flush=True)
+        return None
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "batch64":
+        return bench_batch(args)
+    if args.workload in ("adjoint64", "lgrad"):
+        return bench_side(args)
+    if args.workload == "d2q9":
+        return bench_d2q9(args)
+
+    import torch
+
+    rank, world, local = dist_setup(args)
+    spec = workload_spec(args.workload)
+    if args.storage:
+        spec["storage"] = args.storage
+        spec["label"] = spec["label"].replace(
+            "FP32", args.storage.upper() + (" weight-shifted storage, FP32 arithmetic" if args.storage in ("fp16", "bf16")
+                                            else " storage"))
+    r = channel_cycles(spec, args, rank, world, local, args.steps)
+    lat, N = r["lat"], r["N"]
+    ms_per_step = r["ms"] / args.steps
+    value = whole_job_mlups(world, N, STEPS_PER_CYCLE * args.steps, r["ms"])
+    state_gb = BYTES_PER_NODE[spec["storage"]] * N / 1e9
+    e2e = None if args.no_e2e else end_to_end(args, lat, r["snaps"], N, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if spec["storage"] == "fp32" else spec["storage"], "data": "synthetic",
         "config": {"workload": spec["label"], "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
-                   "l2": "inputs > L2 (1.4 GB of state per LBM step), no flush",
-                   "state_finite_after_run": ok},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "one LBM step: " + PASS_KERNELS[sp], "bytes_per_node": bpn,
-                     "traffic_note": TRAFFIC_NOTE.get(sp),
-                     "step_ms": step_ms},
+                   "l2": f"inputs > L2 ({state_gb:.1f} GB of state per LBM step), no flush",
+                   "state_finite_after_run": r["ok"]},
+        "roofline": roofline_of(spec, args, N, r["step_ms"]),
         "e2e": e2e,
-        "gpu_launches": launches,
-        "clocks": clk,
+        "gpu_launches": r["launches"],
+        "clocks": r["clk"],
     }
     if rank == 0 and world == 1:
-        line["lattice_gradient"] = lattice_gradient_report(lat, dev[0]["g6"])
-        line["transform_interp"] = transform_interp_report(lat, dev, w["layout"])
+        line["lattice_gradient"] = lattice_gradient_report(lat, r["dev"][0]["g6"])
+        line["transform_interp"] = transform_interp_report(lat, r["dev"], r["w"]["layout"])
+    del lat, r
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.workload == "target256" and not args.no_secondary:
+        # the dynamic channel of the plain FP32 form, beside the target line
+        s2 = workload_spec("dynamic")
+        if args.storage:
+            s2["storage"] = args.storage
+        r2 = channel_cycles(s2, args, rank, world, local, max(3, args.steps // 2))
+        k2 = max(3, args.steps // 2)
+        line["dynamic_channel"] = {"workload": s2["label"], "value": whole_job_mlups(1, r2["N"], STEPS_PER_CYCLE * k2,
+                                                                                    r2["ms"]),
+                                   "unit": UNIT, "ms_per_step": r2["ms"] / k2, "steps": k2,
+                                   "roofline": roofline_of(s2, args, r2["N"], r2["step_ms"]),
+                                   "state_finite_after_run": r2["ok"]}
+        del r2
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(args.step_kernel)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
