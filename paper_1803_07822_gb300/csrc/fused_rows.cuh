@@ -11,15 +11,16 @@
 //   2. steps tile t_{k-m}, m iterations behind, exactly as k_step_rows does
 //      (two stages).
 // Warps: 8 compute warps; a copy warp for the momentum stage; a copy warp
-// for the step stages, which before staging a step tile checks with one
-// acquire load that the momentum tiles holding its rho u rows are published;
-// and a publishing warp, which stores each momentum tile from shared memory
-// with one bulk copy, waits for its completion and counts its iteration as
-// published (release).  So no compute warp fences or waits on another CTA.
-// With m >= ceil((nyb + 1) / G) + 1 the tiles a step needs were formed at
-// least one iteration earlier by every CTA, and the populations the step
-// reads were pulled through L2 a few iterations before: HBM sees them once
-// per step.
+// for the step stages, which before staging a step tile checks with acquire
+// loads (one lane per tile) that each of the up to nine momentum tiles
+// holding its rho u rows carries this launch's stamp; and a publishing warp,
+// which stores each momentum tile from shared memory with one bulk copy,
+// waits for its completion and stamps the tile as published (release).  So
+// no compute warp fences or waits on another CTA, and a step tile waits only
+// for the CTAs that formed its neighbours, never for all of them.  With
+// m >= ceil((nyb + 1) / G) + 1 the tiles a step needs were formed at least
+// one iteration earlier, and the populations the step reads were pulled
+// through L2 a few iterations before: HBM sees them once per step.
 //
 // rho u of a face node follows from its inner node without the boundary
 // rule's populations: a wall or inflow node takes rho_i u_w (the first
@@ -234,36 +235,31 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
 {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
-// Publication count: every CTA publishes its momentum tiles in order, and
-// cnt[k] counts the CTAs that have published iteration k (a CTA past its
-// last tile still counts the remaining iterations).  After this launch's
-// publication of iteration k, cnt[k] = epoch * G (mod 2^32), epoch being the
-// number of fused launches so far.  A step tile needs every momentum tile
-// up to the largest one holding its rho u rows, i.e. cnt[k_dep] at target.
-__device__ __forceinline__ int dep_iteration(const Lat& L, const Plan& pl, int t, int G)
+// Publication stamps: done[t] holds the number of the last fused launch
+// (epoch, counted from 1) whose momentum tile t is stored.  The step of tile
+// t reads the rho u rows of the tiles (plane zt + dz, row block yb + dy),
+// dz, dy in {-1, 0, 1}; dep_tile gives the k-th of them (k = 3 (dz + 1) +
+// (dy + 1)), or -1 where that is no tile (a face plane, written by the tiles
+// of plane zt; a y block past a non-periodic end; k >= 9).
+__device__ __forceinline__ int dep_tile(const Lat& L, const Plan& pl, int t, int k)
 {
+    if (k >= 9) return -1;
     const int nz = pl.ntiles / pl.nyb;
     const int zt = t / pl.nyb, yb = t - zt * pl.nyb;
-    const bool yper = L.bclo[1] == BC_PERIODIC;
-    int tmax = t;
-    for (int dz = -1; dz <= 1; dz++) {
-        const int z2 = zt + dz;
-        if (z2 < 0 || z2 >= nz) continue;  // a face plane: written by the tiles of plane zt
-        for (int dy = -1; dy <= 1; dy++) {
-            int y2 = yb + dy;
-            if (y2 < 0 || y2 >= pl.nyb) {
-                if (!yper) continue;
-                y2 = y2 < 0 ? y2 + pl.nyb : y2 - pl.nyb;
-            }
-            tmax = max(tmax, z2 * pl.nyb + y2);
-        }
+    const int z2 = zt + k / 3 - 1;
+    int y2 = yb + k % 3 - 1;
+    if (z2 < 0 || z2 >= nz) return -1;
+    if (y2 < 0 || y2 >= pl.nyb) {
+        if (L.bclo[1] != BC_PERIODIC) return -1;
+        y2 = y2 < 0 ? y2 + pl.nyb : y2 - pl.nyb;
     }
-    return tmax / G;
+    return z2 * pl.nyb + y2;
 }
 __device__ __forceinline__ bool reached(unsigned v, unsigned target) { return (int)(v - target) >= 0; }
 
@@ -320,10 +316,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
     } else if (warp == NW + 1) {
         // step copy warp
         const Pol pol = make_pol();
-        const unsigned target = epoch * (unsigned)G;
-        unsigned pre = 0;  // cnt of the next tile's dependency, loaded ahead
         int ks = 0;
-        if (lane == 0 && K > 0) pre = ld_acquire(done + dep_iteration(L, pl, b, G));
         for (; ks < K; ks++) {
             const int s = ks & 1, t = b + ks * G;
             if (ks >= 2) {
@@ -331,26 +324,23 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
             unsigned char* st = smem_fused + (size_t)s * pl.stage_bytes;
-            // the momentum tiles this step reads must be published: one
-            // acquire load of their iteration's count (loaded ahead for the
-            // next tile), checked before any copy of the tile is in flight
+            // the momentum tiles this step reads must be published: lane k
+            // waits for neighbour k of the tile to carry this launch's stamp,
+            // before any copy of the tile is in flight
             int dep = 1;
-            if (lane == 0) {
-                if (!reached(pre, target)) {
-                    const unsigned* c = done + dep_iteration(L, pl, t, G);
-                    const unsigned long long t0 = now_ns();
-                    while (!reached(ld_acquire(c), target))
-                        if (now_ns() - t0 > wait_ns) {
-                            dep = 0;
-                            break;
-                        }
-                }
-                asm volatile("fence.proxy.async.global;\n" ::: "memory");
+            const int dt = dep_tile(L, pl, t, lane);
+            if (dt >= 0) {
+                const unsigned long long t0 = now_ns();
+                while (!reached(ld_acquire(done + dt), epoch))
+                    if (now_ns() - t0 > wait_ns) {
+                        dep = 0;
+                        break;
+                    }
             }
-            dep = __shfl_sync(0xffffffffu, dep, 0);
+            dep = __all_sync(0xffffffffu, dep);
+            asm volatile("fence.proxy.async.global;\n" ::: "memory");
             issue_tile<S>(L, pl, &M.pop, &M.pop3, &M.jf, &M.jf3, &M.geo, &M.hist, t, st, &fullS[s], Pin, jf, lane,
                           dep ? (PART_MAIN | PART_JF) : PART_MAIN, pol);
-            if (lane == 0 && ks + 1 < K) pre = ld_acquire(done + dep_iteration(L, pl, t + G, G));
             __syncwarp();
             if (lane == 0) bar_arrive(&fullS[s]);
             if (!dep) {
@@ -368,7 +358,6 @@ __global__ void __launch_bounds__(NTHR_F, 1)
         // from shared memory to HBM, then the count of its iteration; a CTA
         // past its last tile counts the remaining iterations
         const bool yper = L.bclo[1] == BC_PERIODIC;
-        const int Kmax = (pl.ntiles + G - 1) / G;
         const unsigned long long keep = policy_evict_last();
         int it = 0;
         for (; it < K; it++) {
@@ -394,13 +383,10 @@ __global__ void __launch_bounds__(NTHR_F, 1)
                 bar_arrive(&jsFree[bb]);
                 asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
                 asm volatile("fence.proxy.async.global;\n" ::: "memory");
-                if (!(b == 0 && it == withhold)) red_release_add(done + it, 1u);
+                if (!(b == 0 && it == withhold)) st_release(done + t, epoch);
             }
             __syncwarp();
         }
-        if (it == K && lane == 0)
-            for (int k = K; k < Kmax; k++)
-                if (!(b == 0 && k == withhold)) red_release_add(done + k, 1u);
     } else {
         // compute warps
         const unsigned long long pol_store = policy_evict_first();
