@@ -450,9 +450,10 @@ int launch_fused_step(cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* e
     unsigned epoch = R.epoch + 1;  // fused launches including this one; the counts wrap with it
     const int G = pl.ntiles < c->n_sm ? pl.ntiles : c->n_sm;
     // lookahead: the momentum tiles a step tile needs lie at most
-    // ceil((nyb + 1) / G) iterations ahead on any CTA; the slack of four more
-    // absorbs the publication latency (measured best on GB300)
-    int m = (pl.nyb + 1 + G - 1) / G + 5;
+    // ceil((nyb + 1) / G) iterations ahead on any CTA; two more absorb the
+    // publication latency (a sweep of 1, 2, 4, 7 more on GB300 at 256^3 with
+    // per-tile stamps: 1.351, 1.178, 1.199, 1.247 ms per step)
+    int m = (pl.nyb + 1 + G - 1) / G + 3;
     unsigned off_m = R.off_m, off_sg = R.off_sg, off_h4 = R.off_h4, off_js = R.off_js;
     Mom4<float>* jf = (Mom4<float>*)c->jf;
     unsigned* done = R.done;
