@@ -318,8 +318,10 @@ def oracle_batch_sample(ws, count=3, steps=10):
 def bench_batch(args):
     """The batched form: 64 independent periodic channels with sides drawn from
     U{32..96} per axis, 4-mode deformations of 2-10 % amplitude, tau in
-    [0.55, 1.0], FP32, all advanced by two launches per LBM step replayed from
-    a CUDA graph, block size from the library's autotuner.  A bench step is 10
+    [0.55, 1.0], FP32, all advanced by one persistent launch per LBM step (a
+    device-side queue of work items over every channel, a grid barrier
+    between the momentum and step phases) replayed from a CUDA graph, tile
+    shape from the library's autotuner.  A bench step is 10
     LBM steps of every channel.  Also timed: the same channels stepped one
     channel at a time (each its own launches), the per-channel baseline."""
     import torch
@@ -331,7 +333,7 @@ def bench_batch(args):
     for i, w in enumerate(ws):
         b[i].set_chart(w["chart"])
         b[i].init_equilibrium()
-    tb, tune_ms = b.tune(reps=5)
+    shape, tune_table = b.tune(reps=5)
     stream = b.stream
     N = b.nodes
 
@@ -384,15 +386,17 @@ def bench_batch(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "64 independent deformed periodic channels, sides U{32..96}, 4 modes 2-10 %, "
-                               "tau U[0.55, 1.0], FP32, batched (one momentum + one step launch per LBM step, "
-                               "CUDA graph)", "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
-                   "l2": "inputs > L2 (1.4 GB of state per LBM step), no flush", "block_nodes": tb,
-                   "tune_ms_per_lbm_step": tune_ms, "state_finite_after_run": not bad, "unstable_channels": bad},
+                               "tau U[0.55, 1.0], FP32, batched (one persistent launch per LBM step over a "
+                               "work-item queue, CUDA graph)", "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
+                   "l2": "inputs > L2 (5.8 GB of state per LBM step), no flush",
+                   "tile_shape": {"block_nodes": shape[0], "item_nodes": shape[1], "blocks_per_sm": shape[2]},
+                   "tune_ms_per_lbm_step": {f"{k[0]}/{k[1]}/{k[2]}": v for k, v in sorted(tune_table.items())},
+                   "state_finite_after_run": not bad and b.check(), "unstable_channels": bad},
         "per_channel_launches": {"value": world * N * STEPS_PER_CYCLE / (ms_pc * 1e-3) / 1e6, "unit": UNIT,
                                  "ms_per_step": ms_pc},
         "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "one batched LBM step: k_batch_momentum + k_batch_step", "bytes_per_node": 332},
+                     "kernel": "one batched LBM step: k_batch_persistent", "bytes_per_node": 332},
         "e2e": {"value": world * N * STEPS_PER_CYCLE / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 8 * len(masses)},
         "gpu_launches": launches,

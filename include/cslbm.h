@@ -343,16 +343,36 @@ cslbm_status cslbm_batch_create(int nb, const cslbm_params* p, void* workspace, 
 cslbm_status cslbm_batch_context(cslbm_batch* b, int i, cslbm_ctx** out);
 
 /* nsteps time steps of every channel (Sec. II, Eqs. collision and streaming,
- * per channel): two launches per step (momentum pass and step pass over all
- * channels' nodes), replayed two steps at a time from a CUDA graph.
- * Asynchronous; ESTATE when a channel has no state. */
+ * per channel): ONE persistent launch per step over all channels, whose CTAs
+ * (all resident: a cooperative launch) take runs of nodes from a device-side
+ * queue for the momentum field, meet at a grid barrier, then take the step's
+ * runs from a second queue; two steps are replayed at a time from a CUDA
+ * graph.  Asynchronous; ESTATE when a channel has no state. */
 cslbm_status cslbm_batch_step(cslbm_batch* b, int nsteps);
 
-/* Autotuner: times the nodes-per-block candidates (128, 256, 512) on this
- * batch, reps repetitions of one step from the current state each (the state
- * does not advance), keeps the fastest and returns it in *block_nodes and
- * the per-step times in ms[3] (either may be null).  Synchronises. */
-cslbm_status cslbm_batch_tune(cslbm_batch* b, int reps, int* block_nodes, float* ms);
+/* Autotuner of the batch step's tile shape: times every candidate -- nodes
+ * per block (128, 256, 512) x nodes per work item (1, 4, 16 blocks) x blocks
+ * per SM (the resident maximum and half of it) -- on this batch, reps
+ * repetitions of one step from the current state each (the state does not
+ * advance), keeps the fastest and returns it in shape3 = {nodes per block,
+ * nodes per work item, blocks per SM} and its time per step in *ms (either
+ * may be null).  Synchronises. */
+cslbm_status cslbm_batch_tune(cslbm_batch* b, int reps, int* shape3, float* ms);
+
+/* Set the batch step's tile shape {nodes per block, nodes per work item,
+ * blocks per SM} by hand; EINVAL unless nodes per block is 128, 256 or 512,
+ * nodes per work item a power of two in 128..8192 that it divides, and
+ * blocks per SM between 1 and the number that can be resident. */
+cslbm_status cslbm_batch_set_shape(cslbm_batch* b, const int* shape3);
+
+/* The last tuning's candidates: *count of them; the first `max` shapes (3 ints
+ * each, as cslbm_batch_tune returns them) and times per step (ms) copied out. */
+cslbm_status cslbm_batch_tune_results(const cslbm_batch* b, int max, int* shapes, float* ms, int* count);
+
+/* CSLBM_ETIMEOUT (once, then the flag is cleared) when the grid barrier of a
+ * batch step ran out of its bounded wait (half a second), CSLBM_OK
+ * otherwise.  Synchronises the batch's stream. */
+cslbm_status cslbm_batch_check(cslbm_batch* b);
 
 /* Kernels launched by cslbm_batch_step so far (graph replays included). */
 cslbm_status cslbm_batch_launches(const cslbm_batch* b, long long* launches);

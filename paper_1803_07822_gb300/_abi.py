@@ -83,6 +83,9 @@ SIGNATURES = {
     "cslbm_batch_context": [_P, _I, ctypes.POINTER(_P)],
     "cslbm_batch_step": [_P, _I],
     "cslbm_batch_tune": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)],
+    "cslbm_batch_tune_results": [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I)],
+    "cslbm_batch_check": [_P],
+    "cslbm_batch_set_shape": [_P, ctypes.POINTER(_I)],
     "cslbm_batch_launches": [_P, ctypes.POINTER(ctypes.c_longlong)],
     "cslbm_batch_destroy": [_P],
     "cslbm2d_workspace_bytes": [ctypes.POINTER(Params2D), ctypes.POINTER(_SZ)],

@@ -323,12 +323,33 @@ class CurvedBatch:
         call("cslbm_batch_step", self.batch, int(nsteps))
 
     def tune(self, reps=10):
-        """Pick the nodes per block by timing the candidates on this batch;
-        returns (chosen, {candidate: ms per step})."""
-        tb = ctypes.c_int(0)
-        ms = (ctypes.c_float * 3)()
-        call("cslbm_batch_tune", self.batch, int(reps), ctypes.byref(tb), ms)
-        return tb.value, {128: ms[0], 256: ms[1], 512: ms[2]}
+        """Pick the tile shape (nodes per block, nodes per work item, blocks
+        per SM) by timing the candidates on this batch; returns (chosen,
+        {candidate: ms per step})."""
+        shape = (ctypes.c_int * 3)()
+        best = ctypes.c_float(0.0)
+        call("cslbm_batch_tune", self.batch, int(reps), shape, ctypes.byref(best))
+        n = ctypes.c_int(0)
+        call("cslbm_batch_tune_results", self.batch, 0, None, None, ctypes.byref(n))
+        shapes = (ctypes.c_int * (3 * n.value))()
+        ms = (ctypes.c_float * n.value)()
+        call("cslbm_batch_tune_results", self.batch, n.value, shapes, ms, ctypes.byref(n))
+        table = {tuple(shapes[3 * i:3 * i + 3]): ms[i] for i in range(n.value)}
+        return tuple(shape[:]), table
+
+    def set_shape(self, shape):
+        """Tile shape (nodes per block, nodes per work item, blocks per SM) by hand."""
+        call("cslbm_batch_set_shape", self.batch, (ctypes.c_int * 3)(*shape))
+
+    def check(self):
+        """True unless a batch step's grid barrier ran out of time (cleared by this call)."""
+        lib = _abi.load()
+        st = lib.cslbm_batch_check(self.batch)
+        if st == _abi.ETIMEOUT:
+            return False
+        if st != _abi.OK:
+            raise _abi.CslbmError(st, "cslbm_batch_check", lib.cslbm_last_error().decode())
+        return True
 
     def launches(self):
         k = ctypes.c_longlong(0)

@@ -1,6 +1,7 @@
-"""Batched form: independent channels of uneven sizes advanced by two kernel
-launches per step (CUDA graph), against the FP64 oracle channel by channel
-and against the same channels stepped one by one."""
+"""Batched form: independent channels of uneven sizes advanced by one
+persistent launch per step (work-item queue, grid barrier, CUDA graph),
+against the FP64 oracle channel by channel and against the same channels
+stepped one by one; the tile-shape tuner."""
 import numpy as np
 import pytest
 
@@ -70,19 +71,42 @@ def test_batch_equals_channels_stepped_alone_with_metric_update():
         r1, u1 = b[i].moments()
         r2, u2 = solo[i].moments()
         assert rel(r1, r2) < 1e-6 and rel(u1, u2) < 1e-5, i
-    assert b.launches() >= 2 * 19
+    assert b.launches() == 19  # one persistent launch per step
+    assert b.check()
 
 
-def test_tune_picks_a_block_size_and_keeps_the_state():
+def test_tune_picks_a_tile_shape_and_keeps_the_state():
     ws = small_batch(4)
     b = make_batch(ws)
     b.step(3)
     before = [c.moments() for c in b]
-    tb, ms = b.tune(reps=3)
-    assert tb in (128, 256, 512) and all(v > 0 for v in ms.values())
+    shape, table = b.tune(reps=3)
+    assert shape in table and len(table) >= 9
+    assert {s[0] for s in table} == {128, 256, 512} and all(v > 0 for v in table.values())
+    assert all(s[1] % s[0] == 0 and s[2] >= 1 for s in table)
+    assert table[shape] == min(table.values())
     after = [c.moments() for c in b]
     for (r1, u1), (r2, u2) in zip(before, after):
         assert np.array_equal(r1, r2) and np.array_equal(u1, u2)
+    # every shape steps the same state to the same result
+    from paper_1803_07822_gb300.lattice import CurvedBatch  # noqa: F401
     b.step(2)
-    assert all(c.check() for c in b)
+    assert all(c.check() for c in b) and b.check()
 
+
+@pytest.mark.parametrize("shape_index", [0, -1])
+def test_batch_result_does_not_depend_on_the_tile_shape(shape_index):
+    """The work-item queue hands out runs of nodes in any order and size; the
+    per-node arithmetic is the same, so two tile shapes give the same bits."""
+    ws = small_batch(4)
+    a, c = make_batch(ws), make_batch(ws)
+    _, table = a.tune(reps=1)
+    shapes = sorted(table)
+    a.set_shape(shapes[shape_index])
+    c.set_shape(shapes[len(shapes) // 2])
+    a.step(9)
+    c.step(9)
+    for i in range(len(ws)):
+        r1, u1 = a[i].moments()
+        r2, u2 = c[i].moments()
+        assert np.array_equal(r1, r2) and np.array_equal(u1, u2), i

@@ -101,8 +101,9 @@ def test_target_256_cube_sampled_windows():
 def test_full_batch_of_64_sampled_channels():
     """The benchmark's batch at its full size and in its launch
     configuration: 64 channels with sides drawn from U{32..96}, 4-mode
-    deformations of 2-10 %, tau in [0.55, 1.0], the block size picked by the
-    autotuner, steps replayed from the CUDA graph; 20 steps from a
+    deformations of 2-10 %, tau in [0.55, 1.0], the tile shape picked by the
+    autotuner, one persistent launch per step replayed from the CUDA graph;
+    20 steps from a
     developed-flow state (so that u is well conditioned), then the smallest,
     the largest and one more channel against the oracle over the whole
     channel, with mass."""
