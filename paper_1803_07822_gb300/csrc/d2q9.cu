@@ -454,6 +454,203 @@ __global__ void __launch_bounds__(TB, 4) k2_step(Lat L, const R* __restrict__ P,
     for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
 }
 
+// ---------------------------------------------------------------------------
+// The step in one pass: a block owns a BX x BY tile of nodes and forms rho u
+// of the tile and of the ring of nodes around it into shared memory
+// (recomputing the ring, which neighbouring blocks form too, instead of
+// writing a rho u field to HBM and reading it back), then steps its nodes
+// with the gradient stencil read from shared memory.  A stencil site past a
+// non-periodic face takes the linear ghost 2 j(face) - j(face - n) of sites
+// that are in the tile or its ring.  The pulled slots of a node are read
+// once, kept in registers between the two phases.
+// ---------------------------------------------------------------------------
+constexpr int BX = 32, BY = 8, RX = BX + 2, RY = BY + 2, NRING = RX * RY - BX * BY;
+
+// tile-local (lx, ly) in [-1, BX] x [-1, BY] of the tile at (x0, y0):
+// inside the lattice after periodic wrapping, or a ghost
+__device__ __forceinline__ bool tile_site_in(const Lat& L, int x0, int y0, int lx, int ly)
+{
+    int gx = x0 + lx, gy = y0 + ly;
+    return wrap(L, 0, gx) && wrap(L, 1, gy);
+}
+
+// rho u at tile-local (lx, ly), ghosts extrapolated axis by axis
+template <class R>
+__device__ __forceinline__ void tile_j(const Lat& L, const R (*jt)[RY][RX], int x0, int y0, int lx, int ly, R out[2])
+{
+    int xs[2], ys[2];
+    R wx[2], wy[2];
+    int mx = 1, my = 1;
+    const int gx = x0 + lx, gy = y0 + ly;
+    xs[0] = lx;
+    wx[0] = R(1);
+    if (gx < 0 && L.lo[0] != PER) { xs[0] = lx + 1; xs[1] = lx + 2; wx[0] = R(2); wx[1] = R(-1); mx = 2; }
+    else if (gx >= L.n[0] && L.hi[0] != PER) { xs[0] = lx - 1; xs[1] = lx - 2; wx[0] = R(2); wx[1] = R(-1); mx = 2; }
+    ys[0] = ly;
+    wy[0] = R(1);
+    if (gy < 0 && L.lo[1] != PER) { ys[0] = ly + 1; ys[1] = ly + 2; wy[0] = R(2); wy[1] = R(-1); my = 2; }
+    else if (gy >= L.n[1] && L.hi[1] != PER) { ys[0] = ly - 1; ys[1] = ly - 2; wy[0] = R(2); wy[1] = R(-1); my = 2; }
+    out[0] = out[1] = R(0);
+    for (int b = 0; b < my; b++)
+        for (int a = 0; a < mx; a++) {
+            const R w = wx[a] * wy[b];
+            out[0] += w * jt[0][ys[b] + 1][xs[a] + 1];
+            out[1] += w * jt[1][ys[b] + 1][xs[a] + 1];
+        }
+}
+
+// the forcing coefficients of a node from its moments, geometry and the
+// lattice gradient D[k][i] = d_k (rho u^i) (Eqs. forcing-A/B/C); fe returns
+// f^eq - w
+template <class R>
+__device__ __forceinline__ void forcing_from_gradient(const Lat& L, const Geo<R>& g, R rho, const R j[2],
+                                                      const R Pi[3], const R D[2][2], R fe[Q], R out[NF])
+{
+    feq_all<R>(g, R(L.theta), rho, j, fe);
+    R Peq[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        const R c0 = R(cx(l)), c1 = R(cy(l)), fl = fe[l];
+        Peq[0] += fl * c0 * c0;
+        Peq[1] += fl * c0 * c1;
+        Peq[2] += fl * c1 * c1;
+    }
+    Peq[0] = g.sg * (Peq[0] + R(1.0 / 3.0));
+    Peq[1] = g.sg * Peq[1];
+    Peq[2] = g.sg * (Peq[2] + R(1.0 / 3.0));
+    R T[2][2];
+    const R kv = R(L.kvisc);
+    T[0][0] = Peq[0] + kv * (Pi[0] - Peq[0]);
+    T[0][1] = T[1][0] = Peq[1] + kv * (Pi[1] - Peq[1]);
+    T[1][1] = Peq[2] + kv * (Pi[2] - Peq[2]);
+    auto gam = [&](int i, int a, int b) { return g.gam[i][s3(a, b)]; };
+    auto gi = [&](int a, int b) { return g.gi[s3(a, b)]; };
+    const R theta = R(L.theta);
+    R A = R(0);
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = 0; k < 2; k++) A -= gam(i, i, k) * j[k] + gam(k, i, k) * j[i];
+    R B[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        R b = R(L.fext[i]);
+#pragma unroll
+        for (int jj = 0; jj < 2; jj++)
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                b -= gam(k, jj, k) * T[i][jj] + gam(i, jj, k) * T[jj][k] + gam(jj, jj, k) * T[k][i];
+        B[i] = b;
+    }
+    R bard[2][2], cov[2][2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const R trace = gam(0, k, 0) + gam(1, k, 1);
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            bard[k][i] = D[k][i] - trace * j[i];
+            cov[k][i] = D[k][i] + gam(i, k, 0) * j[0] + gam(i, k, 1) * j[1];
+        }
+    }
+    const R divbar = bard[0][0] + bard[1][1], divcov = cov[0][0] + cov[1][1];
+    R C[3];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int jj = i; jj < 2; jj++) {
+            R sc = R(1.0 / 3.0) * (bard[jj][i] + bard[i][jj] + (i == jj ? divbar : R(0)));
+#pragma unroll
+            for (int k = 0; k < 2; k++) sc -= theta * (cov[k][i] * gi(jj, k) + cov[k][jj] * gi(i, k));
+            sc -= theta * divcov * gi(i, jj);
+            C[s3(i, jj)] = sc;
+        }
+    out[0] = A;
+    out[1] = B[0];
+    out[2] = B[1];
+    out[3] = C[0];
+    out[4] = C[1];
+    out[5] = C[2];
+}
+
+template <class R>
+__global__ void __launch_bounds__(BX * BY, 4) k2_step_tile(Lat L, const R* __restrict__ P, R* __restrict__ Pout,
+                                                        const R* __restrict__ Fc, R* __restrict__ Fout,
+                                                        const R* __restrict__ G)
+{
+    __shared__ R jt[2][RY][RX];
+    const long long N = L.N;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool mine = x < L.n[0] && y < L.n[1];
+    const long long v = x + (long long)L.n[0] * y;
+    // phase 1: rho u of the tile's own nodes (their state kept) ...
+    R h[Q], Fo[NF], rho = R(1), j[2] = {R(0), R(0)}, Pi[3] = {R(0), R(0), R(0)};
+    if (mine) {
+        node_state<R>(L, P, Fc, G, x, y, h, Fo);
+        moments_h<R>(h, G[v], Fo, rho, j, Pi);
+        jt[0][ty + 1][tx + 1] = j[0];
+        jt[1][ty + 1][tx + 1] = j[1];
+    }
+    // ... and of the ring around the tile (sites inside the lattice only)
+    for (int k = threadIdx.x; k < NRING; k += BX * BY) {
+        int lx, ly;
+        if (k < RX) { lx = k - 1; ly = -1; }
+        else if (k < 2 * RX) { lx = k - RX - 1; ly = BY; }
+        else { const int r = k - 2 * RX; ly = r >> 1; lx = (r & 1) ? BX : -1; }
+        int gx = x0 + lx, gy = y0 + ly;
+        // a site of the ring may also lie past the lattice's far end without
+        // a wrap (a ragged last tile): it is a ghost or unused then
+        if (!(wrap(L, 0, gx) && wrap(L, 1, gy))) continue;
+        if (gx >= L.n[0] || gy >= L.n[1]) continue;
+        const long long u = gx + (long long)L.n[0] * gy;
+        R hh[Q], FF[NF], rr, jj[2], PP[3];
+        node_state<R>(L, P, Fc, G, gx, gy, hh, FF);
+        moments_h<R>(hh, G[u], FF, rr, jj, PP);
+        jt[0][ly + 1][lx + 1] = jj[0];
+        jt[1][ly + 1][lx + 1] = jj[1];
+    }
+    // tile nodes past a ragged end are stencil sites of their neighbours too
+    if (!mine && tx < BX && ty < BY) {
+        int gx = x, gy = y;
+        if (wrap(L, 0, gx) && wrap(L, 1, gy) && gx < L.n[0] && gy < L.n[1] && (gx != x || gy != y)) {
+            const long long u = gx + (long long)L.n[0] * gy;
+            R hh[Q], FF[NF], rr, jj[2], PP[3];
+            node_state<R>(L, P, Fc, G, gx, gy, hh, FF);
+            moments_h<R>(hh, G[u], FF, rr, jj, PP);
+            jt[0][ty + 1][tx + 1] = jj[0];
+            jt[1][ty + 1][tx + 1] = jj[1];
+        }
+    }
+    __syncthreads();
+    if (!mine) return;
+    // phase 2: the step of the tile's nodes
+    R D[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
+#pragma unroll
+    for (int l = 1; l < Q; l++) {
+        R jn[2];
+        tile_j<R>(L, jt, x0, y0, tx + cx(l), ty + cy(l), jn);
+        const R w = R(3.0 * wq(l));
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            D[0][i] += w * R(cx(l)) * jn[i];
+            D[1][i] += w * R(cy(l)) * jn[i];
+        }
+    }
+    Geo<R> g;
+    load_geo(G, N, v, g);
+    R Fn[NF], fe[Q];
+    forcing_from_gradient<R>(L, g, rho, j, Pi, D, fe, Fn);
+    const R om = R(L.omega);
+    R K[NF];
+#pragma unroll
+    for (int k = 0; k < NF; k++) K[k] = Fn[k] - R(0.5) * om * Fo[k];
+#pragma unroll
+    for (int l = 0; l < Q; l++) Pout[l * N + v] = (R(1) - om) * h[l] + om * fe[l] + forcing_l<R>(l, g.isg, K);
+#pragma unroll
+    for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
+}
+
 // initialisation: slots so that the gather returns f^eq with no forcing yet
 template <class R>
 __global__ void __launch_bounds__(TB) k2_init_eq(Lat L, const double* __restrict__ rho0, const double* __restrict__ u0,
@@ -840,10 +1037,9 @@ template <class R> void step_once(cslbm2d_ctx* c)
 {
     const Lat L = lat_of(c);
     const int i = c->pc, o = 1 - c->pc;
-    k2_momentum<R><<<nb(c->N), TB, 0, c->stream>>>(L, (const R*)c->P[i], (const R*)c->F[i], (const R*)c->G[c->gc],
-                                                   (R*)c->jf);
-    k2_step<R><<<nb(c->N), TB, 0, c->stream>>>(L, (const R*)c->P[i], (R*)c->P[o], (const R*)c->F[i], (R*)c->F[o],
-                                               (const R*)c->G[c->gc], (const R*)c->jf);
+    const dim3 grid((unsigned)((L.n[0] + BX - 1) / BX), (unsigned)((L.n[1] + BY - 1) / BY));
+    k2_step_tile<R><<<grid, BX * BY, 0, c->stream>>>(L, (const R*)c->P[i], (R*)c->P[o], (const R*)c->F[i],
+                                                     (R*)c->F[o], (const R*)c->G[c->gc]);
     c->pc = o;
 }
 
