@@ -403,12 +403,16 @@ cslbm_status cslbm_update_metric(cslbm_ctx* c, const double* g6, const double* d
 {
     if (!c || !g6 || !dg18 || !Jnew9) return fail(CSLBM_EINVAL, "null argument");
     if (!c->has_state) return fail(CSLBM_ESTATE, "update_metric before init_equilibrium");
-    if (cslbm_status s = run_metric(c, g6, dg18, on_device, 1 - c->gc, false)) return s;
     if (on_device) {
-        c->ops->transform(c, Jnew9, c->N, 0, c->N);
+        // metric and transformation in one pass
+        int* bad = (int*)(c->scratch + 32);
+        if (!c->metric_check_pending) CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+        c->ops->chart_change(c, g6, dg18, Jnew9, bad);
         c->launches++;
-        LAUNCH_CHECK("transform kernel");
+        LAUNCH_CHECK("chart-change kernel");
+        c->metric_check_pending = 1;
     } else {
+        if (cslbm_status s = run_metric(c, g6, dg18, on_device, 1 - c->gc, false)) return s;
         for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
             long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
             if (cslbm_status s = stage_in(c, Jnew9, 9, v0, cnt, c->staging)) return s;

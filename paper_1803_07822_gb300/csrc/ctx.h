@@ -92,6 +92,10 @@ struct cslbm_ops {
     // chart change for nodes [v0, v0+cnt): P[pc],H[hc],G[gc] -> P[1-pc],H[1-hc] with G[1-gc]
     void (*transform)(const cslbm_ctx*, const double* Jnew, long long stride, long long v0,
                       long long cnt);
+    // the whole node-wise chart change in one pass (device inputs of every
+    // node): G[1-gc] from g6/dg18, then P[pc],H[hc] -> P[1-pc],H[1-hc] and J
+    // replaced by Jnew; *bad set non-zero on det g <= 0
+    void (*chart_change)(const cslbm_ctx*, const double* g6, const double* dg18, const double* Jnew, int* bad);
     // chart change with interpolation: the transformation inputs of every node
     // into scratch [20][N] (precision R), then every node of P[1-pc],H[1-hc]
     // from them at psi3 [3][N] (old lattice coordinates) with G[1-gc]; J (old)

@@ -35,23 +35,19 @@ template <class R> __device__ __forceinline__ R to_real(double x);
 template <> __device__ __forceinline__ float to_real<float>(double x) { return f64_to_f32_rn(x); }
 template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
 
+// geometry of node v (G[.][v]: sqrt(g), g^ij, Gamma) from its metric g6 /
+// dg18 at entry t of the inputs (stride apart); returns false for det g <= 0
 template <class R>
-__global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, const double* __restrict__ dg18,
-                                                long long stride, long long v0, long long cnt, R* __restrict__ geo,
-                                                long long N, int* bad)
+__device__ __forceinline__ bool metric_node(const double* __restrict__ g6, const double* __restrict__ dg18,
+                                            long long stride, long long t, R* __restrict__ geo, long long N,
+                                            long long v, R& sg_out)
 {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    long long v = v0 + t;
     const double a = g6[0 * stride + t], b = g6[1 * stride + t], c = g6[2 * stride + t];
     const double d = g6[3 * stride + t], e = g6[4 * stride + t], f = g6[5 * stride + t];
     // g = [[a b c] [b d e] [c e f]]
     const double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
     const double det = a * A + b * B + c * C;
-    if (!(det > 0.0)) {
-        atomicOr(bad, 1);
-        return;
-    }
+    if (!(det > 0.0)) return false;
     // 1/det and sqrt(det) in FP64.  For FP32-and-narrower storage they start
     // from FP32 estimates refined by one Newton step each (relative error
     // ~1e-14 before the rounding to R), which spares the FP64 divide and
@@ -81,7 +77,8 @@ __global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, c
     R dg[3][6], gr[6];
 #pragma unroll
     for (int m = 0; m < 6; m++) gr[m] = to_real<R>(gi[m]);
-    geo[v] = to_real<R>(sd);
+    sg_out = to_real<R>(sd);
+    geo[v] = sg_out;
 #pragma unroll
     for (int k = 0; k < 6; k++) geo[(1 + k) * N + v] = gr[k];
 #pragma unroll
@@ -99,6 +96,18 @@ __global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, c
                 for (int l = 0; l < 3; l++) s += gr[s6(i, l)] * (dg[j][s6(k, l)] + dg[k][s6(j, l)] - dg[l][s6(j, k)]);
                 geo[(7 + i * 6 + s6(j, k)) * N + v] = R(0.5) * s;
             }
+    return true;
+}
+
+template <class R>
+__global__ void __launch_bounds__(TPB) k_metric(const double* __restrict__ g6, const double* __restrict__ dg18,
+                                                long long stride, long long v0, long long cnt, R* __restrict__ geo,
+                                                long long N, int* bad)
+{
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    R sg;
+    if (!metric_node<R>(g6, dg18, stride, t, geo, N, v0 + t, sg)) atomicOr(bad, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -459,6 +468,46 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
     transform_store<S, R>(L, Pout, hout, geo_new[v], x, y, z, v, Dp, in[0], j, M2, in[10], B, Cs, literal);
 }
 
+// The whole node-wise chart change in one pass (device inputs): the new
+// geometry of the node from its metric (as k_metric), then the
+// transformation of its state (as k_transform) with the new sqrt(g) from
+// registers.  The metric's FP64 arithmetic overlaps the transformation's
+// memory traffic instead of running as a pass of its own.
+template <class S, class R>
+__global__ void __launch_bounds__(TPB) k_chart(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+                                               const R* __restrict__ hin, R* __restrict__ hout,
+                                               const R* __restrict__ geo_old, R* __restrict__ geo_new,
+                                               double* __restrict__ J, const double* __restrict__ g6,
+                                               const double* __restrict__ dg18, const double* __restrict__ Jnew,
+                                               int literal, int* bad)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= L.N) return;
+    R sgn;
+    if (!metric_node<R>(g6, dg18, L.N, v, geo_new, L.N, v, sgn)) {
+        atomicOr(bad, 1);
+        return;
+    }
+    int x, y, z;
+    node_coords(L, v, x, y, z);
+    R in[20];
+    transform_inputs<S, R>(L, Pin, hin, geo_old, x, y, z, v, literal, in);
+    double Jo[9], Jn[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        Jo[k] = J[k * L.N + v];
+        Jn[k] = Jnew[k * L.N + v];
+    }
+    R Dp[3][3];
+    dphi<R, R>(Jn, Jo, Dp);
+#pragma unroll
+    for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
+    const R j[3] = {in[1], in[2], in[3]}, B[3] = {in[11], in[12], in[13]};
+    const R M2[6] = {in[4], in[5], in[6], in[7], in[8], in[9]};
+    const R Cs[6] = {in[14], in[15], in[16], in[17], in[18], in[19]};
+    transform_store<S, R>(L, Pout, hout, sgn, x, y, z, v, Dp, in[0], j, M2, in[10], B, Cs, literal);
+}
+
 // Chart change with interpolation, pass 1: the transformation inputs of every
 // old node into mf [20][N]
 template <class S, class R>
@@ -751,6 +800,12 @@ template <class S, class R> struct Launch {
                                                                H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, Jnew,
                                                                stride, v0, cnt, c->p.transform_flags & 1);
     }
+    static void chart_change(const cslbm_ctx* c, const double* g6, const double* dg18, const double* Jnew, int* bad)
+    {
+        k_chart<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc),
+                                                           H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, g6,
+                                                           dg18, Jnew, c->p.transform_flags & 1, bad);
+    }
     static void transform_interp(const cslbm_ctx* c, const double* Jnew, const double* psi3, void* scratch)
     {
         const int lit = c->p.transform_flags & 1;
@@ -785,7 +840,7 @@ template <class S, class R> struct Launch {
     static constexpr cslbm_ops ops()
     {
         return cslbm_ops{&metric, &init_scatter, &momentum_field, &step, &half_shift,
-                         &transform, &transform_interp, &readout, &mass, &wall_force, &check};
+                         &transform, &chart_change, &transform_interp, &readout, &mass, &wall_force, &check};
     }
 };
 

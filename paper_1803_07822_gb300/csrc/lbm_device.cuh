@@ -276,12 +276,64 @@ __device__ __forceinline__ bool on_boundary(const Lat& L, int x, int y, int z)
            (L.bclo[2] != BC_PERIODIC && (z == 0 || z == L.n[2] - 1));
 }
 
+// The boundary rule (reading of Sec. IV.A / VI.A: nodes on the wall) from
+// the inner node's pulled populations si = h - w, metric Gi and history Hi:
+// non-equilibrium extrapolation for wall and inflow nodes (velocity uw,
+// contravariant), zero-gradient copy for outflow nodes, both scaled by
+// sqrt(g_inner) / sqrt(g_node); returns the node's s = h - w with h = f -
+// F'/2 from its own history Hw and metric Gw.
+template <class R>
+__device__ __forceinline__ void boundary_rule(const Lat& L, int bc, const R si[Q], const Geo<R>& Gi, const Hist<R>& Hi,
+                                              const Geo<R>& Gw, const Hist<R>& Hw, const R uw[3], R s[Q])
+{
+    const R ratio = Gi.sg * Gw.isg;
+    R fi[Q];
+#pragma unroll
+    for (int l = 0; l < Q; l++) fi[l] = si[l] + R(wq(l)) + R(0.5) * forcing_l(l, Gi.isg, Hi);
+    if (bc == BC_OUTFLOW) {
+#pragma unroll
+        for (int l = 0; l < Q; l++) s[l] = fi[l] * ratio - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
+        return;
+    }
+    R m0, m1[3], m2[6];
+    sums(si, m0, m1, m2);
+    const R rho = Gi.sg * (R(1) + m0) + R(0.5) * Hi.A;
+    R j[3], jw[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) j[a] = Gi.sg * m1[a] + R(0.5) * Hi.B[a];
+#pragma unroll
+    for (int a = 0; a < 3; a++) jw[a] = rho * uw[a];
+    R a2w[6], a2i[6];
+    feq_coeffs(rho, jw, Gw.gi, R(L.theta), a2w);
+    feq_coeffs(rho, j, Gi.gi, R(L.theta), a2i);
+    const R trw = a2w[0] + a2w[3] + a2w[5], tri = a2i[0] + a2i[3] + a2i[5];
+#pragma unroll
+    for (int l = 0; l < Q; l++) {
+        R few = hermite_l(l, Gw.isg, rho, jw, a2w, trw);
+        R fei = hermite_l(l, Gi.isg, rho, j, a2i, tri);
+        R fw = few + (fi[l] - fei) * ratio;
+        s[l] = fw - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
+    }
+}
+
+// the imposed velocity of face (axis, side) at node r (zero without one)
+template <class R>
+__device__ __forceinline__ void face_velocity(const Lat& L, int axis, int side, const int r[3], R uw[3])
+{
+    uw[0] = uw[1] = uw[2] = R(0);
+    const double* fv = L.face[axis * 2 + side];
+    if (fv) {
+        long long fn = face_node(L, axis, r);
+        long long nf = axis == 0 ? (long long)L.n[1] * L.n[2] : (axis == 1 ? (long long)L.n[0] * L.n[2] : (long long)L.n[0] * L.n[1]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) uw[a] = R(fv[a * nf + fn]);
+    }
+}
+
 // Populations s = h - w of a boundary node from the boundary rule applied to
-// its inner node: non-equilibrium extrapolation for wall and inflow nodes,
-// zero-gradient copy for outflow nodes, both scaled by sqrt(g_inner) /
-// sqrt(g_node); h is then f - F'/2 with the node's own history.  Kept out of
-// line where it matters (see boundary_site): it runs for the few nodes on the
-// faces.
+// its inner node (boundary_rule), everything gathered from global memory.
+// Kept out of line where it matters (see boundary_site): it runs for the few
+// nodes on the faces.
 template <class S, class R>
 __device__ __forceinline__ void boundary_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
                                            const R* __restrict__ geo, int x, int y, int z, R s[Q])
@@ -298,41 +350,9 @@ __device__ __forceinline__ void boundary_pops(const Lat& L, const S* __restrict_
     Hist<R> Hi, Hw;
     load_hist(hist, N, vi, Hi);
     load_hist(hist, N, vw, Hw);
-    const R ratio = Gi.sg * Gw.isg;
-    R fi[Q];
-#pragma unroll
-    for (int l = 0; l < Q; l++) fi[l] = si[l] + R(wq(l)) + R(0.5) * forcing_l(l, Gi.isg, Hi);
-    if (bc == BC_OUTFLOW) {
-#pragma unroll
-        for (int l = 0; l < Q; l++) s[l] = fi[l] * ratio - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
-        return;
-    }
-    R m0, m1[3], m2[6];
-    sums(si, m0, m1, m2);
-    const R rho = Gi.sg * (R(1) + m0) + R(0.5) * Hi.A;
-    R j[3], jw[3], uw[3] = {R(0), R(0), R(0)};
-#pragma unroll
-    for (int a = 0; a < 3; a++) j[a] = Gi.sg * m1[a] + R(0.5) * Hi.B[a];
-    const double* fv = L.face[axis * 2 + side];
-    if (fv) {
-        long long fn = face_node(L, axis, r);
-        long long nf = axis == 0 ? (long long)L.n[1] * L.n[2] : (axis == 1 ? (long long)L.n[0] * L.n[2] : (long long)L.n[0] * L.n[1]);
-#pragma unroll
-        for (int a = 0; a < 3; a++) uw[a] = R(fv[a * nf + fn]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++) jw[a] = rho * uw[a];
-    R a2w[6], a2i[6];
-    feq_coeffs(rho, jw, Gw.gi, R(L.theta), a2w);
-    feq_coeffs(rho, j, Gi.gi, R(L.theta), a2i);
-    const R trw = a2w[0] + a2w[3] + a2w[5], tri = a2i[0] + a2i[3] + a2i[5];
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        R few = hermite_l(l, Gw.isg, rho, jw, a2w, trw);
-        R fei = hermite_l(l, Gi.isg, rho, j, a2i, tri);
-        R fw = few + (fi[l] - fei) * ratio;
-        s[l] = fw - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
-    }
+    R uw[3];
+    face_velocity(L, axis, side, r, uw);
+    boundary_rule(L, bc, si, Gi, Hi, Gw, Hw, uw, s);
 }
 
 // Node state: shifted populations s = h - w of any node (boundary nodes
