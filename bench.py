@@ -447,9 +447,9 @@ def bench_side(args):
                     lattice_gradient=r)
         if not args.no_cpu_baseline:
             try:
-                r["cpu_baseline"] = oracle_side_samples(workload_spec("dynamic"))[0]
+                line["cpu_baseline"] = oracle_gradient_sample(workload_spec("dynamic"))
             except Exception as e:  # noqa: BLE001
-                r["cpu_baseline"] = {"error": str(e)[-300:]}
+                line["cpu_baseline"] = {"error": str(e)[-300:]}
     print(json.dumps(line), flush=True)
 
 
@@ -689,13 +689,36 @@ def transform_interp_report(lat, dev, layout, reps=5):
                     "and reads 8 corners per node (20 fields + the FP64 Jacobian)"}
 
 
+def oracle_gradient_sample(spec, order=4):
+    """The FP64 oracle's lattice gradient (App. D) of the six metric
+    components of the channel `spec` at half the extent per axis, in the
+    lattice-gradient line's unit (GFLOP/s, by the same algorithmic FLOP count
+    as the library's figure) and in Mnode/s."""
+    import oracle
+    n = tuple(v // 2 for v in spec["n"])
+    w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
+                          re=spec["re"])
+    (c0, _), = snapshots(w, [500.0])
+    N = int(np.prod(n))
+    pad = [(0 if (lo == 0 and hi == 0) else 1) for lo, hi in zip(w["bc_lo"], w["bc_hi"])]
+    Ne = int(np.prod([k + 2 * p for k, p in zip(n, pad)]))
+    flop = 6 * (LAP_FLOP[order] * Ne + GRAD_FLOP[order] * N)
+    t0 = time.perf_counter()
+    oracle.lattice_gradient(n, c0.g6, order, w["bc_lo"], w["bc_hi"])
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": flop / dt / 1e9, "unit": "GFLOP/s (FP64)", "mnode_per_s": N / dt / 1e6, "cores": cores,
+            "kind": "oracle", "sample": f"order-{order} gradient of the 6 metric components, {n[0]}x{n[1]}x{n[2]} "
+                                        f"crop of the same generator, FP64 oracle ({dt:.2f} s)"}
+
+
 def oracle_side_samples(spec):
     """The FP64 oracle on a half-size crop of the bench channel (the same
     generator at n / 2 per axis): the fourth-order lattice gradient of the six
-    metric components (App. D), and one chart change node-wise and with
-    interpolation (Sec. IV.B) between the snapshots t = 500 and 510.  Returns
-    the cpu_baseline objects of the lattice_gradient and transform_interp
-    reports."""
+    metric components (App. D, oracle_gradient_sample), and one chart change
+    node-wise and with interpolation (Sec. IV.B) between the snapshots t = 500
+    and 510.  Returns the cpu_baseline objects of the lattice_gradient and
+    transform_interp reports."""
     import oracle
     n = tuple(v // 2 for v in spec["n"])
     w = I.dynamic_channel(n=n, seed=spec["seed"], n_modes=spec["n_modes"], amp=spec["amp"], tau=spec["tau"],
@@ -704,9 +727,6 @@ def oracle_side_samples(spec):
     N = int(np.prod(n))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     crop = f"{n[0]}x{n[1]}x{n[2]} crop of the same generator, FP64 oracle"
-    t0 = time.perf_counter()
-    oracle.lattice_gradient(n, c0.g6, 4, w["bc_lo"], w["bc_hi"])
-    dt_grad = time.perf_counter() - t0
     wa = w["layout"][0]
     psi = np.stack(I.grid(n))
     psi[wa] = psi[wa] * c1.J9[wa * 3 + wa] / c0.J9[wa * 3 + wa]
@@ -723,8 +743,7 @@ def oracle_side_samples(spec):
         else:
             o.transform_interp(c1.g6, c1.dg18, c0.J9, c1.J9, psi)
         times[mode] = time.perf_counter() - t0
-    grad = {"value": N / dt_grad / 1e6, "unit": "Mnode/s", "cores": cores, "kind": "oracle",
-            "sample": f"order-4 gradient of the 6 metric components, {crop} ({dt_grad:.2f} s)"}
+    grad = oracle_gradient_sample(spec)
     trans = {"node_wise_ms": times["node"] * 1e3, "interp_ms": times["interp"] * 1e3, "nodes": N, "cores": cores,
              "kind": "oracle", "sample": f"one chart change (metric + transform) on the {crop}"}
     return grad, trans

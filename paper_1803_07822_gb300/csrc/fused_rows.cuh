@@ -424,13 +424,7 @@ __global__ void __launch_bounds__(NTHR_F, 1)
 template <class S>
 int launch_fused_step(cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* err)
 {
-    static bool attr = false;
-    if (!attr) {
-        int max_smem = 0;
-        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-        cudaFuncSetAttribute(rows::k_step_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-        attr = true;
-    }
+    set_smem_optin_once(rows::k_step_fused<S>, c->device);
     cslbm_rows& R = c->rows;
     const rows::Plan& pl = R.plan;
     const S* Pin = (const S*)c->P[pc];

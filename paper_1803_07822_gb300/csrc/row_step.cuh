@@ -27,6 +27,8 @@
 // reports CSLBM_ETIMEOUT) and the CTA leaves after its copies have landed.
 #pragma once
 
+#include <mutex>
+
 #include "flat_step.cuh"
 #include "rows_plan.h"
 
@@ -434,19 +436,29 @@ __global__ void __launch_bounds__(NTHR, 1)
 
 }  // namespace rows
 
+// The opt-in shared-memory limit of a kernel, set once per device: the
+// attribute belongs to the context of the device current when it is set.
+template <class K>
+inline void set_smem_optin_once(K* kernel, int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    if (device < 0 || device >= 64) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return;
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    done[device] = true;
+}
+
 // one time step through the row-staged pass (the context's plan and maps
 // exist): momentum pass, row pass, face nodes.  Returns the number of
 // kernels launched.
 template <class S>
 int launch_rows_step(const cslbm_ctx* c, const Lat& L, int pc, int hc, int gc, int* err)
 {
-    static bool attr = false;
-    if (!attr) {
-        int max_smem = 0;
-        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-        cudaFuncSetAttribute(rows::k_step_rows<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-        attr = true;
-    }
+    set_smem_optin_once(rows::k_step_rows<S>, c->device);
     const cslbm_rows& R = c->rows;
     const rows::Plan& pl = R.plan;
     const S* Pin = (const S*)c->P[pc];
