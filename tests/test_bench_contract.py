@@ -75,7 +75,8 @@ def test_side_report_oracle_samples():
     workload's half-size crop)."""
     b = _bench()
     g, t = b.oracle_side_samples(b.workload_spec("crop64"))
-    assert g["kind"] == "oracle" and g["value"] > 0 and g["unit"] == "Mnode/s" and "32x64x32" in g["sample"]
+    assert g["kind"] == "oracle" and g["value"] > 0 and g["unit"] == "GFLOP/s (FP64)" and "32x64x32" in g["sample"]
+    assert g["mnode_per_s"] > 0
     assert t["kind"] == "oracle" and t["node_wise_ms"] > 0 and t["interp_ms"] > 0 and t["nodes"] == 32 * 64 * 32
 
 
