@@ -958,48 +958,76 @@ def main():
 
 
 def end_to_end(args, lat, snaps, N, world):
-    """The same cycles through the public API with pinned host buffers: the
-    metric inputs and face velocities are copied host -> device and the mass
-    and wall force read back inside the timed region."""
+    """The same cycles through the public API with every cycle's inputs
+    copied from pinned host buffers: the metric, its derivatives, the
+    Jacobian and the face velocities go host -> device on a copy stream into
+    one of two device buffers while the previous cycle computes (the next
+    cycle's chart change waits for its copy), and the mass and wall force are
+    read back every cycle.  All copies and reads are inside the timed
+    region."""
     import torch
+    keys = ("g6", "dg18", "J9")
     pinned = []
-    h2d = 0
     for ch, faces in snaps:
         p = {}
-        for k in ("g6", "dg18", "J9"):
-            t = torch.empty(getattr(ch, k).shape, dtype=torch.float64, pin_memory=True)
-            t.numpy()[...] = getattr(ch, k)
-            p[k] = t.numpy()
+        for k in keys:
+            p[k] = torch.empty(getattr(ch, k).shape, dtype=torch.float64, pin_memory=True)
+            p[k].numpy()[...] = getattr(ch, k)
         p["faces"] = {}
         for key, u in faces.items():
             t = torch.empty(u.shape, dtype=torch.float64, pin_memory=True)
             t.numpy()[...] = u
-            p["faces"][key] = t.numpy()
+            p["faces"][key] = t
         pinned.append(p)
-    h2d = sum(pinned[1][k].nbytes for k in ("g6", "dg18", "J9")) + sum(u.nbytes for u in pinned[1]["faces"].values())
+    h2d = sum(pinned[1][k].numel() * 8 for k in keys) + sum(u.numel() * 8 for u in pinned[1]["faces"].values())
     d2h = 4 * 8
+    dev = [{k: torch.empty_like(pinned[1][k], device="cuda") for k in keys} for _ in range(2)]
+    for d in dev:
+        d["faces"] = {key: torch.empty_like(u, device="cuda") for key, u in pinned[1]["faces"].items()}
+    copy = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    for e in free:
+        e.record(lat.stream)
 
-    def cycle_host(k):
+    def upload(k, slot):
         p = pinned[1 + k % args.snapshots]
-        lat.update_metric(p["g6"], p["dg18"], p["J9"])
-        for (a, s), u in p["faces"].items():
-            lat.set_boundary_velocity(a, s, u)
-        lat.step(STEPS_PER_CYCLE)
-        lat.total_mass()
-        lat.wall_force(0, 1)
+        with torch.cuda.stream(copy):
+            copy.wait_event(free[slot])
+            for name in keys:
+                dev[slot][name].copy_(p[name], non_blocking=True)
+            for key, u in p["faces"].items():
+                dev[slot]["faces"][key].copy_(u, non_blocking=True)
+            ready[slot].record(copy)
 
-    for k in range(2):
-        cycle_host(k)
+    def run(k0, count):
+        upload(k0, k0 % 2)
+        for k in range(k0, k0 + count):
+            slot = k % 2
+            if k + 1 < k0 + count:
+                upload(k + 1, 1 - slot)
+            lat.stream.wait_event(ready[slot])
+            d = dev[slot]
+            lat.update_metric(d["g6"], d["dg18"], d["J9"])
+            for (a, s), u in d["faces"].items():
+                lat.set_boundary_velocity(a, s, u)
+            free[slot].record(lat.stream)
+            lat.step(STEPS_PER_CYCLE)
+            lat.total_mass()
+            lat.wall_force(0, 1)
+
+    run(0, 2)
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        cycle_host(k)
+    run(2, args.steps)
     torch.cuda.synchronize()
     t_e2e = reduce_max(time.perf_counter() - t0, world)
     barrier(world)
     return {"value": world * N * STEPS_PER_CYCLE * args.steps / t_e2e / 1e6, "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "note": "inputs copied host -> device on a second stream, double-buffered, overlapping the previous "
+                    "cycle's steps"}
 
 
 if __name__ == "__main__":

@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
 // registers.  The metric's FP64 arithmetic overlaps the transformation's
 // memory traffic instead of running as a pass of its own.
 template <class S, class R>
-__global__ void __launch_bounds__(TPB) k_chart(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
+__global__ void __launch_bounds__(TPB, 3) k_chart(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
                                                const R* __restrict__ hin, R* __restrict__ hout,
                                                const R* __restrict__ geo_old, R* __restrict__ geo_new,
                                                double* __restrict__ J, const double* __restrict__ g6,
