@@ -424,100 +424,27 @@ __device__ __forceinline__ void forcing_coeffs(const Lat& L, const R* __restrict
     out[5] = C[2];
 }
 
-// collision f* = f - (f - f^eq)/tau + F(t) - F(t - dt)/2 into the node's own
-// slots, the new coefficients into the node's history
-template <class R>
-__global__ void __launch_bounds__(TB, 4) k2_step(Lat L, const R* __restrict__ P, R* __restrict__ Pout,
-                                              const R* __restrict__ Fc, R* __restrict__ Fout,
-                                              const R* __restrict__ G, const R* __restrict__ jf)
-{
-    const long long v = blockIdx.x * (long long)TB + threadIdx.x;
-    if (v >= L.N) return;
-    const long long N = L.N;
-    const int x = (int)(v % L.n[0]), y = (int)(v / L.n[0]);
-    R h[Q], Fo[NF];
-    node_state<R>(L, P, Fc, G, x, y, h, Fo);
-    Geo<R> g;
-    load_geo(G, N, v, g);
-    R rho, j[2], Pi[3], Fn[NF], fe[Q];
-    moments_h<R>(h, g.sg, Fo, rho, j, Pi);
-    forcing_coeffs<R>(L, jf, x, y, g, rho, j, Pi, fe, Fn);
-    // f* - w = (1 - omega) h + omega (f^eq - w) + F(t) - omega F(t - dt)/2, with
-    // s = h + F(t - dt)/2: one recomposition of the combined coefficients
-    const R om = R(L.omega);
-    R K[NF];
-#pragma unroll
-    for (int k = 0; k < NF; k++) K[k] = Fn[k] - R(0.5) * om * Fo[k];
-#pragma unroll
-    for (int l = 0; l < Q; l++) Pout[l * N + v] = (R(1) - om) * h[l] + om * fe[l] + forcing_l<R>(l, g.isg, K);
-#pragma unroll
-    for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
-}
-
-// ---------------------------------------------------------------------------
-// The step in one pass: a block owns a BX x BY tile of nodes and forms rho u
-// of the tile and of the ring of nodes around it into shared memory
-// (recomputing the ring, which neighbouring blocks form too, instead of
-// writing a rho u field to HBM and reading it back), then steps its nodes
-// with the gradient stencil read from shared memory.  A stencil site past a
-// non-periodic face takes the linear ghost 2 j(face) - j(face - n) of sites
-// that are in the tile or its ring.  The pulled slots of a node are read
-// once, kept in registers between the two phases.
-// ---------------------------------------------------------------------------
-constexpr int BX = 32, BY = 8, RX = BX + 2, RY = BY + 2, NRING = RX * RY - BX * BY;
-
-// tile-local (lx, ly) in [-1, BX] x [-1, BY] of the tile at (x0, y0):
-// inside the lattice after periodic wrapping, or a ghost
-__device__ __forceinline__ bool tile_site_in(const Lat& L, int x0, int y0, int lx, int ly)
-{
-    int gx = x0 + lx, gy = y0 + ly;
-    return wrap(L, 0, gx) && wrap(L, 1, gy);
-}
-
-// rho u at tile-local (lx, ly), ghosts extrapolated axis by axis
-template <class R>
-__device__ __forceinline__ void tile_j(const Lat& L, const R (*jt)[RY][RX], int x0, int y0, int lx, int ly, R out[2])
-{
-    int xs[2], ys[2];
-    R wx[2], wy[2];
-    int mx = 1, my = 1;
-    const int gx = x0 + lx, gy = y0 + ly;
-    xs[0] = lx;
-    wx[0] = R(1);
-    if (gx < 0 && L.lo[0] != PER) { xs[0] = lx + 1; xs[1] = lx + 2; wx[0] = R(2); wx[1] = R(-1); mx = 2; }
-    else if (gx >= L.n[0] && L.hi[0] != PER) { xs[0] = lx - 1; xs[1] = lx - 2; wx[0] = R(2); wx[1] = R(-1); mx = 2; }
-    ys[0] = ly;
-    wy[0] = R(1);
-    if (gy < 0 && L.lo[1] != PER) { ys[0] = ly + 1; ys[1] = ly + 2; wy[0] = R(2); wy[1] = R(-1); my = 2; }
-    else if (gy >= L.n[1] && L.hi[1] != PER) { ys[0] = ly - 1; ys[1] = ly - 2; wy[0] = R(2); wy[1] = R(-1); my = 2; }
-    out[0] = out[1] = R(0);
-    for (int b = 0; b < my; b++)
-        for (int a = 0; a < mx; a++) {
-            const R w = wx[a] * wy[b];
-            out[0] += w * jt[0][ys[b] + 1][xs[a] + 1];
-            out[1] += w * jt[1][ys[b] + 1][xs[a] + 1];
-        }
-}
-
 // the forcing coefficients of a node from its moments, geometry and the
-// lattice gradient D[k][i] = d_k (rho u^i) (Eqs. forcing-A/B/C); fe returns
-// f^eq - w
+// lattice gradient D[k][i] = d_k (rho u^i) (Eqs. forcing-A/B/C), and the
+// first two Hermite coefficients of f^eq - w (a0e, a2e; the first is j).
+// The equilibrium flux is Pi^eq = sum_l f^eq_l c c sqrt(g) = rho theta g^ij
+// + j^i j^j / rho: the second moment of the second-order Hermite expansion
+// on D2Q9 (sum w c c = delta / 3, sum w c c c c = (delta delta + 2 perms) / 9)
 template <class R>
 __device__ __forceinline__ void forcing_from_gradient(const Lat& L, const Geo<R>& g, R rho, const R j[2],
-                                                      const R Pi[3], const R D[2][2], R fe[Q], R out[NF])
+                                                      const R Pi[3], const R D[2][2], R& a0e, R a2e[3], R out[NF])
 {
-    feq_all<R>(g, R(L.theta), rho, j, fe);
-    R Peq[3] = {R(0), R(0), R(0)};
+    const R ir = R(1) / rho, theta = R(L.theta);
+    R Peq[3];
 #pragma unroll
-    for (int l = 0; l < Q; l++) {
-        const R c0 = R(cx(l)), c1 = R(cy(l)), fl = fe[l];
-        Peq[0] += fl * c0 * c0;
-        Peq[1] += fl * c0 * c1;
-        Peq[2] += fl * c1 * c1;
-    }
-    Peq[0] = g.sg * (Peq[0] + R(1.0 / 3.0));
-    Peq[1] = g.sg * Peq[1];
-    Peq[2] = g.sg * (Peq[2] + R(1.0 / 3.0));
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int k = i; k < 2; k++) {
+            const R jj = j[i] * j[k] * ir;
+            Peq[s3(i, k)] = rho * theta * g.gi[s3(i, k)] + jj;
+            a2e[s3(i, k)] = rho * (theta * g.gi[s3(i, k)] - (i == k ? R(1.0 / 3.0) : R(0))) + jj;
+        }
+    a0e = rho - g.sg;
     R T[2][2];
     const R kv = R(L.kvisc);
     T[0][0] = Peq[0] + kv * (Pi[0] - Peq[0]);
@@ -525,7 +452,6 @@ __device__ __forceinline__ void forcing_from_gradient(const Lat& L, const Geo<R>
     T[1][1] = Peq[2] + kv * (Pi[2] - Peq[2]);
     auto gam = [&](int i, int a, int b) { return g.gam[i][s3(a, b)]; };
     auto gi = [&](int a, int b) { return g.gi[s3(a, b)]; };
-    const R theta = R(L.theta);
     R A = R(0);
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -572,83 +498,177 @@ __device__ __forceinline__ void forcing_from_gradient(const Lat& L, const Geo<R>
     out[5] = C[2];
 }
 
-template <class R>
-__global__ void __launch_bounds__(BX * BY, 4) k2_step_tile(Lat L, const R* __restrict__ P, R* __restrict__ Pout,
-                                                        const R* __restrict__ Fc, R* __restrict__ Fout,
-                                                        const R* __restrict__ G)
+// ---------------------------------------------------------------------------
+// The step in one pass, marching along y.  A block of SW threads owns a strip
+// of SW - 2 columns (thread t at column x0 - 1 + t; threads 0 and SW - 1 only
+// supply rho u of the two columns beside the strip) and a band of rows, which
+// it walks upwards.  For row c it forms the state and rho u of row c + 1 (the
+// pulled slots, the history, sqrt(g)) into a ring of four rho u rows in shared
+// memory, then steps row c with the gradient stencil read from the ring, the
+// state of row c kept in registers from the iteration before.  Every slot is
+// read once; rho u of the columns beside a strip and of the rows beside a
+// band is formed twice (by both neighbours).  A stencil site past a
+// non-periodic face takes the linear ghost 2 j(face) - j(face - n), axis by
+// axis.
+// ---------------------------------------------------------------------------
+
+// a row index past an end: wrapped on a periodic axis, else false
+__device__ __forceinline__ bool wrap_row(const Lat& L, int& r)
 {
-    __shared__ R jt[2][RY][RX];
-    const long long N = L.N;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool mine = x < L.n[0] && y < L.n[1];
-    const long long v = x + (long long)L.n[0] * y;
-    // phase 1: rho u of the tile's own nodes (their state kept) ...
-    R h[Q], Fo[NF], rho = R(1), j[2] = {R(0), R(0)}, Pi[3] = {R(0), R(0), R(0)};
-    if (mine) {
+    if (r >= 0 && r < L.n[1]) return true;
+    if (L.lo[1] != PER) return false;
+    r += r < 0 ? L.n[1] : -L.n[1];
+    return true;
+}
+
+// h, the history and rho u, Pi of node (x, y).  `fast`: an interior node
+// whose pull sources lie inside the lattice without wrapping
+template <class R>
+__device__ __forceinline__ void march_state(const Lat& L, const R* __restrict__ P, const R* __restrict__ Fc,
+                                            const R* __restrict__ G, int x, int y, bool fast, R h[Q], R Fo[NF],
+                                            R& rho, R j[2], R Pi[3])
+{
+    const long long N = L.N, v = x + (long long)L.n[0] * y;
+    if (fast) {
+        load_fc(Fc, N, v, Fo);
+#pragma unroll
+        for (int l = 0; l < Q; l++) h[l] = P[l * N + v - cx(l) - (long long)L.n[0] * cy(l)];
+    } else {
         node_state<R>(L, P, Fc, G, x, y, h, Fo);
-        moments_h<R>(h, G[v], Fo, rho, j, Pi);
-        jt[0][ty + 1][tx + 1] = j[0];
-        jt[1][ty + 1][tx + 1] = j[1];
     }
-    // ... and of the ring around the tile (sites inside the lattice only)
-    for (int k = threadIdx.x; k < NRING; k += BX * BY) {
-        int lx, ly;
-        if (k < RX) { lx = k - 1; ly = -1; }
-        else if (k < 2 * RX) { lx = k - RX - 1; ly = BY; }
-        else { const int r = k - 2 * RX; ly = r >> 1; lx = (r & 1) ? BX : -1; }
-        int gx = x0 + lx, gy = y0 + ly;
-        // a site of the ring may also lie past the lattice's far end without
-        // a wrap (a ragged last tile): it is a ghost or unused then
-        if (!(wrap(L, 0, gx) && wrap(L, 1, gy))) continue;
-        if (gx >= L.n[0] || gy >= L.n[1]) continue;
-        const long long u = gx + (long long)L.n[0] * gy;
-        R hh[Q], FF[NF], rr, jj[2], PP[3];
-        node_state<R>(L, P, Fc, G, gx, gy, hh, FF);
-        moments_h<R>(hh, G[u], FF, rr, jj, PP);
-        jt[0][ly + 1][lx + 1] = jj[0];
-        jt[1][ly + 1][lx + 1] = jj[1];
-    }
-    // tile nodes past a ragged end are stencil sites of their neighbours too
-    if (!mine && tx < BX && ty < BY) {
-        int gx = x, gy = y;
-        if (wrap(L, 0, gx) && wrap(L, 1, gy) && gx < L.n[0] && gy < L.n[1] && (gx != x || gy != y)) {
-            const long long u = gx + (long long)L.n[0] * gy;
-            R hh[Q], FF[NF], rr, jj[2], PP[3];
-            node_state<R>(L, P, Fc, G, gx, gy, hh, FF);
-            moments_h<R>(hh, G[u], FF, rr, jj, PP);
-            jt[0][ty + 1][tx + 1] = jj[0];
-            jt[1][ty + 1][tx + 1] = jj[1];
+    moments_h<R>(h, G[v], Fo, rho, j, Pi);
+}
+
+// rho u at stencil site (t + dx, row slot of c + dy) of the ring, ghosts
+// past non-periodic faces extrapolated axis by axis; gx is thread t's column
+template <class R, int SW>
+__device__ __forceinline__ void ring_site(const Lat& L, const R (*ring)[2][SW], int t, int gx, int c, int m, int dx,
+                                          int dy, R out[2])
+{
+    // two terms per axis; the second has weight 0 unless the site is a ghost
+    int xa = t + dx, xb = t + dx, ma = m + dy, mb = m + dy;
+    R wxa = R(1), wxb = R(0), wya = R(1), wyb = R(0);
+    const int sx = gx + dx, sy = c + dy;
+    if (sx < 0 && L.lo[0] != PER) { xa = t + dx + 1; xb = t + dx + 2; wxa = R(2); wxb = R(-1); }
+    else if (sx >= L.n[0] && L.hi[0] != PER) { xa = t + dx - 1; xb = t + dx - 2; wxa = R(2); wxb = R(-1); }
+    if (sy < 0 && L.lo[1] != PER) { ma = m + dy + 1; mb = m + dy + 2; wya = R(2); wyb = R(-1); }
+    else if (sy >= L.n[1] && L.hi[1] != PER) { ma = m + dy - 1; mb = m + dy - 2; wya = R(2); wyb = R(-1); }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+        out[i] = wya * (wxa * ring[ma & 3][i][xa] + wxb * ring[ma & 3][i][xb]) +
+                 wyb * (wxa * ring[mb & 3][i][xa] + wxb * ring[mb & 3][i][xb]);
+}
+
+// blocks per SM the register budget is set for: 16 warps (FP32), 8 (FP64)
+template <class R, int SW> constexpr int march_min_blocks() { return (sizeof(R) == 8 ? 256 : 512) / SW; }
+
+template <class R, int SW>
+__global__ void __launch_bounds__(SW, march_min_blocks<R, SW>())
+    k2_step_march(Lat L, const R* __restrict__ P, R* __restrict__ Pout, const R* __restrict__ Fc,
+                  R* __restrict__ Fout, const R* __restrict__ G, int nstrip, int H, int nitems)
+{
+    __shared__ R ring[4][2][SW];
+    const int t = threadIdx.x, n0 = L.n[0], n1 = L.n[1];
+    const long long N = L.N;
+    const bool xper = L.lo[0] == PER;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int s = item % nstrip, band = item / nstrip;
+        const int x0 = s * (SW - 2), ya = band * H, yb = min(n1, ya + H);
+        const int gx = x0 - 1 + t;
+        // the column whose rho u this thread forms (wrapped), -1 for none
+        int mxc = gx;
+        if (gx < 0) mxc = xper ? gx + n0 : -1;
+        else if (gx >= n0) mxc = (gx == n0 && xper) ? 0 : -1;
+        const bool stepper = t >= 1 && t <= SW - 2 && gx < n0;
+        // every column of the strip and its pull sources inside, no face column
+        const bool fastx = x0 >= 2 && x0 + SW <= n0;
+        R h[Q], Fo[NF], rho = R(1), j[2] = {R(0), R(0)}, Pi[3] = {R(0), R(0), R(0)};
+        // ring slot of row ya - 1 + m is m & 3: rows ya - 1 and ya first
+        {
+            int r = ya - 1;
+            if (mxc >= 0 && wrap_row(L, r)) {
+                R hh[Q], FF[NF], rr, jj[2], PP[3];
+                march_state<R>(L, P, Fc, G, mxc, r, fastx && r >= 1 && r <= n1 - 2, hh, FF, rr, jj, PP);
+                ring[0][0][t] = jj[0];
+                ring[0][1][t] = jj[1];
+            }
+            if (mxc >= 0) {
+                march_state<R>(L, P, Fc, G, mxc, ya, fastx && ya >= 1 && ya <= n1 - 2, h, Fo, rho, j, Pi);
+                ring[1][0][t] = j[0];
+                ring[1][1][t] = j[1];
+            }
         }
-    }
-    __syncthreads();
-    if (!mine) return;
-    // phase 2: the step of the tile's nodes
-    R D[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
+        for (int c = ya; c < yb; c++) {
+            const int m = c - ya + 1;
+            // row c + 1 into the ring (its state kept for the next iteration)
+            R hn[Q], Fon[NF], rhon = R(1), jn[2] = {R(0), R(0)}, Pin[3] = {R(0), R(0), R(0)};
+            int r = c + 1;
+            if (mxc >= 0 && wrap_row(L, r)) {
+                march_state<R>(L, P, Fc, G, mxc, r, fastx && r >= 1 && r <= n1 - 2, hn, Fon, rhon, jn, Pin);
+                ring[(m + 1) & 3][0][t] = jn[0];
+                ring[(m + 1) & 3][1][t] = jn[1];
+            }
+            __syncthreads();
+            if (stepper) {
+                const long long v = gx + (long long)n0 * c;
+                Geo<R> g;
+                load_geo(G, N, v, g);
+                R D[2][2] = {{R(0), R(0)}, {R(0), R(0)}};
+                if (fastx && c >= 1 && c <= n1 - 2) {
 #pragma unroll
-    for (int l = 1; l < Q; l++) {
-        R jn[2];
-        tile_j<R>(L, jt, x0, y0, tx + cx(l), ty + cy(l), jn);
-        const R w = R(3.0 * wq(l));
+                    for (int l = 1; l < Q; l++) {
+                        const R w = R(3.0 * wq(l));
+                        const int sl = (m + cy(l)) & 3;
 #pragma unroll
-        for (int i = 0; i < 2; i++) {
-            D[0][i] += w * R(cx(l)) * jn[i];
-            D[1][i] += w * R(cy(l)) * jn[i];
+                        for (int i = 0; i < 2; i++) {
+                            const R jl = ring[sl][i][t + cx(l)];
+                            D[0][i] += w * R(cx(l)) * jl;
+                            D[1][i] += w * R(cy(l)) * jl;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 1; l < Q; l++) {
+                        R jl[2];
+                        ring_site<R, SW>(L, ring, t, gx, c, m, cx(l), cy(l), jl);
+                        const R w = R(3.0 * wq(l));
+#pragma unroll
+                        for (int i = 0; i < 2; i++) {
+                            D[0][i] += w * R(cx(l)) * jl[i];
+                            D[1][i] += w * R(cy(l)) * jl[i];
+                        }
+                    }
+                }
+                R Fn[NF], a0e, a2e[3];
+                forcing_from_gradient<R>(L, g, rho, j, Pi, D, a0e, a2e, Fn);
+                // f* - w = (1 - omega) h + omega (f^eq - w) + F(t) - omega F(t - dt)/2 (s = h
+                // + F(t - dt)/2): one Hermite recomposition of the combined coefficients
+                const R om = R(L.omega);
+                R K[NF];
+#pragma unroll
+                for (int k = 0; k < NF; k++) K[k] = Fn[k] - R(0.5) * om * Fo[k];
+                const R c0 = om * a0e + K[0];
+                const R c1[2] = {om * j[0] + K[1], om * j[1] + K[2]};
+                const R c2[3] = {om * a2e[0] + K[3] - K[0] * R(1.0 / 3.0), om * a2e[1] + K[4],
+                                 om * a2e[2] + K[5] - K[0] * R(1.0 / 3.0)};
+#pragma unroll
+                for (int l = 0; l < Q; l++) Pout[l * N + v] = (R(1) - om) * h[l] + hermite<R>(l, g.isg, c0, c1, c2);
+#pragma unroll
+                for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
+            }
+#pragma unroll
+            for (int l = 0; l < Q; l++) h[l] = hn[l];
+#pragma unroll
+            for (int k = 0; k < NF; k++) Fo[k] = Fon[k];
+            rho = rhon;
+            j[0] = jn[0];
+            j[1] = jn[1];
+            Pi[0] = Pin[0];
+            Pi[1] = Pin[1];
+            Pi[2] = Pin[2];
         }
+        __syncthreads();  // the ring is free for the next item
     }
-    Geo<R> g;
-    load_geo(G, N, v, g);
-    R Fn[NF], fe[Q];
-    forcing_from_gradient<R>(L, g, rho, j, Pi, D, fe, Fn);
-    const R om = R(L.omega);
-    R K[NF];
-#pragma unroll
-    for (int k = 0; k < NF; k++) K[k] = Fn[k] - R(0.5) * om * Fo[k];
-#pragma unroll
-    for (int l = 0; l < Q; l++) Pout[l * N + v] = (R(1) - om) * h[l] + om * fe[l] + forcing_l<R>(l, g.isg, K);
-#pragma unroll
-    for (int k = 0; k < NF; k++) Fout[k * N + v] = Fn[k];
 }
 
 // initialisation: slots so that the gather returns f^eq with no forcing yet
@@ -946,6 +966,7 @@ struct cslbm2d_ctx {
     double* stage;    // host-input staging, 10 N doubles
     double* scratch;  // 64 doubles
     int pc, gc, has_state, has_metric;
+    int march_blocks;  // resident blocks of the marching step (0: not yet known)
 };
 
 namespace {
@@ -1033,13 +1054,38 @@ template <class R> cslbm_status metric(cslbm2d_ctx* c, const double* g3, const d
     return CSLBM_OK;
 }
 
+// Work items of the marching step: strips of SW - 2 columns times bands of H
+// rows, H chosen so that the rounds of resident blocks times the rows a block
+// forms (H + 2) are fewest
+constexpr int SW = 64;
+
 template <class R> void step_once(cslbm2d_ctx* c)
 {
     const Lat L = lat_of(c);
     const int i = c->pc, o = 1 - c->pc;
-    const dim3 grid((unsigned)((L.n[0] + BX - 1) / BX), (unsigned)((L.n[1] + BY - 1) / BY));
-    k2_step_tile<R><<<grid, BX * BY, 0, c->stream>>>(L, (const R*)c->P[i], (R*)c->P[o], (const R*)c->F[i],
-                                                     (R*)c->F[o], (const R*)c->G[c->gc]);
+    if (!c->march_blocks) {
+        int dev = 0, nsm = 1, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2_step_march<R, SW>, SW, 0);
+        c->march_blocks = (per > 0 ? per : 1) * nsm;
+    }
+    const int nstrip = (L.n[0] + SW - 3) / (SW - 2), n1 = L.n[1];
+    long long best = -1;
+    int H = n1;
+    for (int nb = 1; nb <= n1; nb++) {
+        const int h = (n1 + nb - 1) / nb, bands = (n1 + h - 1) / h;
+        const long long items = (long long)nstrip * bands;
+        const long long cost = (items + c->march_blocks - 1) / c->march_blocks * (h + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            H = h;
+        }
+    }
+    const int nitems = nstrip * ((n1 + H - 1) / H);
+    const int grid = nitems < c->march_blocks ? nitems : c->march_blocks;
+    k2_step_march<R, SW><<<grid, SW, 0, c->stream>>>(L, (const R*)c->P[i], (R*)c->P[o], (const R*)c->F[i],
+                                                     (R*)c->F[o], (const R*)c->G[c->gc], nstrip, H, nitems);
     c->pc = o;
 }
 
