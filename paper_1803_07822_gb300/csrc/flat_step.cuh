@@ -384,27 +384,26 @@ __global__ void __launch_bounds__(128) k_step_faces(const __grid_constant__ Lat 
                                                     const R* __restrict__ hin, R* __restrict__ hout,
                                                     const R* __restrict__ geo, const Mom4<R>* __restrict__ jf)
 {
-    const long long i = blockIdx.x * 128LL + threadIdx.x;
-    if (i >= f.start[f.nseg]) return;
+    // face nodes number fewer than 2^31 (the lattice's nodes do)
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    if (i >= (int)f.start[f.nseg]) return;
     // segment of node i, by selects over the six (no indexing of f by a
     // runtime value, which would copy it to local memory)
-    int lo0 = 0, lo1 = 0, lo2 = 0, len0 = 1, len1 = 1;
-    long long st = 0;
+    int lo0 = 0, lo1 = 0, lo2 = 0, len0 = 1, len1 = 1, st = 0;
 #pragma unroll
     for (int k = 0; k < 6; k++)
-        if (k < f.nseg && i >= f.start[k]) {
+        if (k < f.nseg && i >= (int)f.start[k]) {
             lo0 = f.lo[k][0];
             lo1 = f.lo[k][1];
             lo2 = f.lo[k][2];
             len0 = f.len[k][0];
             len1 = f.len[k][1];
-            st = f.start[k];
+            st = (int)f.start[k];
         }
-    const long long r = i - st;
-    const long long q = r / len0;
-    const int x = lo0 + (int)(r - q * len0);
-    const int y = lo1 + (int)(q % len1);
-    const int z = lo2 + (int)(q / len1);
+    const int r = i - st, q = r / len0;
+    const int x = lo0 + (r - q * len0);
+    const int y = lo1 + q % len1;
+    const int z = lo2 + q / len1;
     step_boundary_body<S, R>(L, Pin, Pout, hin, hout, geo, jf, x, y, z);
 }
 

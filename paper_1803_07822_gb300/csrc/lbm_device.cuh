@@ -286,34 +286,45 @@ template <class R>
 __device__ __forceinline__ void boundary_rule(const Lat& L, int bc, const R si[Q], const Geo<R>& Gi, const Hist<R>& Hi,
                                               const Geo<R>& Gw, const Hist<R>& Hw, const R uw[3], R s[Q])
 {
+    // Written out, the rule is
+    //   outflow:       s_l = ratio f_l(i) - F_l(w)/2 - w_l,
+    //   wall, inflow:  s_l = feq_l(rho_i, rho_i u_w; w) + ratio (f_l(i) - feq_l(rho_i, j_i; i))
+    //                        - F_l(w)/2 - w_l,
+    // with f_l(i) = si_l + w_l + F_l(i)/2 and ratio = sqrt(g_i) / sqrt(g_w).  Every
+    // feq_l and F_l is w_l / sqrt(g) P_l(b0, b1, b2) of its node, P_l(b) = b0 + 3 b1.c
+    // + 4.5 (b2 : c c - tr b2 / 3) linear in b, and ratio / sqrt(g_i) = 1 / sqrt(g_w),
+    // so the terms combine into one expansion:
+    //   s_l = ratio si_l + (ratio - 1) w_l + w_l / sqrt(g_w) P_l(E),
+    //   E = ((A, B, b2)_i - (A, B, b2)_w) / 2   (b2 = C - c_s^2 delta A of the histories)
+    //     + (0, j_w - j_i, a2eq_w - a2eq_i)     (wall and inflow nodes only; rho cancels).
     const R ratio = Gi.sg * Gw.isg;
-    R fi[Q];
+    const R e0 = R(0.5) * (Hi.A - Hw.A);
+    R e1[3], e2[6];
 #pragma unroll
-    for (int l = 0; l < Q; l++) fi[l] = si[l] + R(wq(l)) + R(0.5) * forcing_l(l, Gi.isg, Hi);
-    if (bc == BC_OUTFLOW) {
+    for (int a = 0; a < 3; a++) e1[a] = R(0.5) * (Hi.B[a] - Hw.B[a]);
 #pragma unroll
-        for (int l = 0; l < Q; l++) s[l] = fi[l] * ratio - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
-        return;
+    for (int k = 0; k < 6; k++) e2[k] = R(0.5) * (Hi.C[k] - Hw.C[k]) - ((k == 0 || k == 3 || k == 5) ? e0 * R(1.0 / 3.0) : R(0));
+    if (bc != BC_OUTFLOW) {
+        R m0, m1[3], m2[6];
+        sums(si, m0, m1, m2);
+        const R rho = Gi.sg * (R(1) + m0) + R(0.5) * Hi.A;
+        R j[3], jw[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            j[a] = Gi.sg * m1[a] + R(0.5) * Hi.B[a];
+            jw[a] = rho * uw[a];
+        }
+        R a2w[6], a2i[6];
+        feq_coeffs(rho, jw, Gw.gi, R(L.theta), a2w);
+        feq_coeffs(rho, j, Gi.gi, R(L.theta), a2i);
+#pragma unroll
+        for (int a = 0; a < 3; a++) e1[a] += jw[a] - j[a];
+#pragma unroll
+        for (int k = 0; k < 6; k++) e2[k] += a2w[k] - a2i[k];
     }
-    R m0, m1[3], m2[6];
-    sums(si, m0, m1, m2);
-    const R rho = Gi.sg * (R(1) + m0) + R(0.5) * Hi.A;
-    R j[3], jw[3];
+    const R tr = e2[0] + e2[3] + e2[5];
 #pragma unroll
-    for (int a = 0; a < 3; a++) j[a] = Gi.sg * m1[a] + R(0.5) * Hi.B[a];
-#pragma unroll
-    for (int a = 0; a < 3; a++) jw[a] = rho * uw[a];
-    R a2w[6], a2i[6];
-    feq_coeffs(rho, jw, Gw.gi, R(L.theta), a2w);
-    feq_coeffs(rho, j, Gi.gi, R(L.theta), a2i);
-    const R trw = a2w[0] + a2w[3] + a2w[5], tri = a2i[0] + a2i[3] + a2i[5];
-#pragma unroll
-    for (int l = 0; l < Q; l++) {
-        R few = hermite_l(l, Gw.isg, rho, jw, a2w, trw);
-        R fei = hermite_l(l, Gi.isg, rho, j, a2i, tri);
-        R fw = few + (fi[l] - fei) * ratio;
-        s[l] = fw - R(0.5) * forcing_l(l, Gw.isg, Hw) - R(wq(l));
-    }
+    for (int l = 0; l < Q; l++) s[l] = ratio * si[l] + (ratio - R(1)) * R(wq(l)) + hermite_l(l, Gw.isg, e0, e1, e2, tr);
 }
 
 // the imposed velocity of face (axis, side) at node r (zero without one)
