@@ -348,27 +348,47 @@ __device__ __forceinline__ void transform_store(const Lat& L, S* __restrict__ Po
         Hn.C[5] += Hn.A * R(1.0 / 3.0);
     }
     const R isgn = R(1) / sgn;
-    const R trP2 = P2[0] + P2[3] + P2[5];
     hout[v] = Hn.A;
 #pragma unroll
     for (int a = 0; a < 3; a++) hout[(1 + a) * L.N + v] = Hn.B[a];
 #pragma unroll
     for (int a = 0; a < 6; a++) hout[(4 + a) * L.N + v] = Hn.C[a];
+    // f~ - F~/2 - w with f~ - w = w/sqrt(g~) P_l(rho - sqrt g~, j~, Pi~ - c_s^2 rho delta) and
+    // F~ = w/sqrt(g~) P_l(A, B, C - c_s^2 delta A): one expansion of the difference
+    R b1[3], b2[6];
+    const R b0 = rho - sgn - R(0.5) * Hn.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) b1[a] = j2[a] - R(0.5) * Hn.B[a];
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        b2[k] = P2[k] - R(0.5) * (Hn.C[k] - ((k == 0 || k == 3 || k == 5) ? Hn.A * R(1.0 / 3.0) : R(0)));
+    const R trb2 = b2[0] + b2[3] + b2[5];
+    // the slot of population l is that of the node r - c_l, which pulls it;
+    // none past a non-periodic face.  Offsets of r - c per axis:
+    const int r0[3] = {x, y, z};
+    unsigned off[3][3], okm = 0u, stride = 1u;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+#pragma unroll
+        for (int c = -1; c <= 1; c++) {
+            int q = r0[a] - c;
+            bool in = q >= 0 && q < L.n[a];
+            if (!in && (q < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) {
+                q = wrapc(q, L.n[a]);
+                in = true;
+            }
+            off[a][c + 1] = in ? (unsigned)q * stride : 0u;
+            okm |= in ? 1u << (3 * a + c + 1) : 0u;
+        }
+        stride *= (unsigned)L.n[a];
+    }
 #pragma unroll
     for (int l = 0; l < Q; l++) {
-        int r[3] = {x - cvec(l, 0), y - cvec(l, 1), z - cvec(l, 2)};
-        bool ok = true;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (r[a] < 0 || r[a] >= L.n[a]) {
-                if ((r[a] < 0 ? L.bclo[a] : L.bchi[a]) == BC_PERIODIC) r[a] = wrapc(r[a], L.n[a]);
-                else ok = false;
-            }
-        }
-        if (!ok) continue;
-        // f~ - F~/2 - w  with  f~ - w = w/sqrt(g~) [(rho - sqrt g~) + ...]
-        R val = hermite_l(l, isgn, rho - sgn, j2, P2, trP2) - R(0.5) * forcing_l(l, isgn, Hn);
-        Store<S>::st(Pout + (long long)pslot(l) * L.N + nidx(L, r[0], r[1], r[2]), val);
+        const int cx = cvec(l, 0) + 1, cy = cvec(l, 1) + 1, cz = cvec(l, 2) + 1;
+        const unsigned need = (1u << cx) | (1u << (3 + cy)) | (1u << (6 + cz));
+        if ((okm & need) != need) continue;
+        const R val = hermite_l(l, isgn, b0, b1, b2, trb2);
+        Store<S>::st(Pout + (long long)pslot(l) * L.N + (off[2][cz] + off[1][cy] + off[0][cx]), val);
     }
 }
 

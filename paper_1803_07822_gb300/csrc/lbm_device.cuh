@@ -204,13 +204,19 @@ __device__ __forceinline__ int wrapc(int v, int n)
 template <class S, class R>
 __device__ __forceinline__ void gather_raw(const Lat& L, const S* __restrict__ P, int x, int y, int z, R s[Q])
 {
+    // the wrapped offsets of r - c per axis, summed per population
+    const unsigned n0 = L.n[0], n01 = n0 * (unsigned)L.n[1];
+    unsigned ox[3], oy[3], oz[3];
 #pragma unroll
-    for (int l = 0; l < Q; l++) {
-        int xs = wrapc(x - cvec(l, 0), L.n[0]);
-        int ys = wrapc(y - cvec(l, 1), L.n[1]);
-        int zs = wrapc(z - cvec(l, 2), L.n[2]);
-        s[l] = R(Store<S>::ld(P + (long long)pslot(l) * L.N + nidx(L, xs, ys, zs)));
+    for (int c = -1; c <= 1; c++) {
+        ox[c + 1] = (unsigned)wrapc(x - c, L.n[0]);
+        oy[c + 1] = (unsigned)wrapc(y - c, L.n[1]) * n0;
+        oz[c + 1] = (unsigned)wrapc(z - c, L.n[2]) * n01;
     }
+#pragma unroll
+    for (int l = 0; l < Q; l++)
+        s[l] = R(Store<S>::ld(P + (long long)pslot(l) * L.N +
+                              (oz[cvec(l, 2) + 1] + oy[cvec(l, 1) + 1] + ox[cvec(l, 0) + 1])));
 }
 
 // Boundary classification: rule of the highest-priority face the node lies on
