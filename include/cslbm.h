@@ -110,7 +110,10 @@ cslbm_status cslbm_destroy(cslbm_ctx* ctx);
 cslbm_status cslbm_set_metric(cslbm_ctx* ctx, const double* g6, const double* dg18, int on_device);
 
 /* Set the chart Jacobian J9 used for Cartesian readout, wall forces and the
- * next chart change.  No transformation of f. */
+ * next chart change.  No transformation of f.  The library keeps the Jacobian
+ * at the precision of its arithmetic: FP64 for FP64 storage, else rounded to
+ * FP32 (the precision D phi is formed in); the same holds for the Jnew9 of
+ * every chart change. */
 cslbm_status cslbm_set_jacobian(cslbm_ctx* ctx, const double* J9, int on_device);
 
 /* Chart change (Sec. IV.B): the metric update of cslbm_set_metric for the new

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "ctx.h"
+#include "fp_convert.h"
 
 namespace {
 
@@ -88,7 +89,7 @@ Layout layout(const cslbm_params* p)
     for (int k = 0; k < 2; k++) { L.off_P[k] = o; o += al(19 * L.N * L.s_bytes); }
     for (int k = 0; k < 2; k++) { L.off_H[k] = o; o += al(10 * L.N * L.r_bytes); }
     for (int k = 0; k < 2; k++) { L.off_G[k] = o; o += al(25 * L.N * L.r_bytes); }
-    L.off_J = o; o += al(9 * L.N * sizeof(double));
+    L.off_J = o; o += al(9 * L.N * L.r_bytes);
     L.off_jf = o; o += al(4 * L.N * L.r_bytes);
     for (int k = 0; k < 6; k++) {
         int a = k / 2;
@@ -121,6 +122,29 @@ cslbm_status fill(cslbm_ctx* c, void* p, long long n, double v, bool fp64)
     if (fp64) k_fill<<<nb, 256, 0, c->stream>>>((double*)p, n, v);
     else k_fillf<<<nb, 256, 0, c->stream>>>((float*)p, n, (float)v);
     LAUNCH_CHECK("fill");
+    return CSLBM_OK;
+}
+
+// components k = 0..8 of cnt nodes from src [9][sstride] (FP64) into the stored
+// Jacobian at nodes v0.., rounded to FP32 on the integer units unless the
+// context computes in FP64 (the rounding of the chart-change kernels)
+__global__ void k_store_jac(const double* __restrict__ src, long long sstride, void* __restrict__ J, long long N,
+                            long long v0, long long cnt, int fp64)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    for (int k = 0; k < 9; k++) {
+        const double x = src[k * sstride + t];
+        if (fp64) ((double*)J)[k * N + v0 + t] = x;
+        else ((float*)J)[k * N + v0 + t] = cslbm::f64_to_f32_rn(x);
+    }
+}
+
+cslbm_status store_jacobian(cslbm_ctx* c, const double* src, long long sstride, long long v0, long long cnt)
+{
+    k_store_jac<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(src, sstride, c->J, c->N, v0, cnt,
+                                                                      c->r_bytes == 8);
+    LAUNCH_CHECK("Jacobian store");
     return CSLBM_OK;
 }
 
@@ -303,7 +327,7 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
         c->H[k] = b + L.off_H[k];
         c->G[k] = b + L.off_G[k];
     }
-    c->J = (double*)(b + L.off_J);
+    c->J = b + L.off_J;
     c->jf = b + L.off_jf;
     for (int k = 0; k < 6; k++) {
         int a = k / 2;
@@ -324,7 +348,7 @@ cslbm_status cslbm_create(const cslbm_params* p, void* ws, size_t bytes, void* s
     if (!s) s = set_flat(c, 1);
     if (!s) {
         for (int i : {0, 4, 8}) {
-            s = fill(c, c->J + (size_t)i * c->N, c->N, 1.0, true);
+            s = fill(c, (char*)c->J + (size_t)i * c->N * c->r_bytes, c->N, 1.0, c->r_bytes == 8);
             if (s) break;
         }
     }
@@ -382,7 +406,7 @@ cslbm_status cslbm_update_metric_interp(cslbm_ctx* c, const double* g6, const do
     c->ops->transform_interp(c, Jnew9, psi3, scratch);
     c->launches += 2;
     LAUNCH_CHECK("interpolating transform kernels");
-    CUDA_TRY(cudaMemcpyAsync(c->J, Jnew9, 9 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (cslbm_status s = store_jacobian(c, Jnew9, c->N, 0, c->N)) return s;
     c->pc ^= 1;
     c->hc ^= 1;
     c->gc ^= 1;
@@ -392,9 +416,13 @@ cslbm_status cslbm_update_metric_interp(cslbm_ctx* c, const double* g6, const do
 cslbm_status cslbm_set_jacobian(cslbm_ctx* c, const double* J9, int on_device)
 {
     if (!c || !J9) return fail(CSLBM_EINVAL, "null argument");
-    CUDA_TRY(cudaMemcpyAsync(c->J, J9, 9 * c->N * sizeof(double),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (on_device) return store_jacobian(c, J9, c->N, 0, c->N);
+    for (long long v0 = 0; v0 < c->N; v0 += c->chunk) {
+        const long long cnt = c->N - v0 < c->chunk ? c->N - v0 : c->chunk;
+        if (cslbm_status s = stage_in(c, J9, 9, v0, cnt, c->staging)) return s;
+        if (cslbm_status s = store_jacobian(c, c->staging, cnt, v0, cnt)) return s;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
     return CSLBM_OK;
 }
 

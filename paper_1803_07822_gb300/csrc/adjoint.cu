@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) k_adj_pull(Lat L, const R* __restrict__ l
 // rule), history, geometry and chart Jacobian
 template <class R>
 __global__ void __launch_bounds__(128) k_adj_seed_force(Lat L, const R* __restrict__ P, const R* __restrict__ H,
-                                                         const R* __restrict__ geo, const double* __restrict__ J,
+                                                         const R* __restrict__ geo, const R* __restrict__ J,
                                                          int axis, int side, double e0, double e1, double e2,
                                                          Bufs<R> B, R* __restrict__ lHo)
 {
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(128) k_adj_seed_force(Lat L, const R* __restri
         double a = 0.0;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-            a += e[b] * J[(b * 3 + i) * N + v];
+            a += e[b] * double(J[(b * 3 + i) * N + v]);
             B.lJ[(b * 3 + i) * N + v] += sgn * double(sg) * e[b] * double(Tn[i]);
         }
         lTn[i] = R(sgn * double(sg) * a);
@@ -544,7 +544,7 @@ template <class R> void seed(cslbm_ctx* c, int axis, int side, const double e[3]
     const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
     const long long nf = (long long)c->n[a1] * c->n[a2];
     k_adj_seed_force<R><<<nb(nf, 128), 128, 0, c->stream>>>(L, (const R*)c->P[c->pc], (const R*)c->H[c->hc],
-                                                            (const R*)c->G[c->gc], c->J, axis, side, e[0], e[1], e[2],
+                                                            (const R*)c->G[c->gc], (const R*)c->J, axis, side, e[0], e[1], e[2],
                                                             B, B.lH[lp]);
     finish_step<R>(c, L, B, lp);
 }

@@ -48,7 +48,8 @@ struct cslbm_ctx {
     void* P[2];      // [19][N] stored populations (pull layout, weight shifted)
     void* H[2];      // [10][N] forcing-history coefficients
     void* G[2];      // [25][N] geometry: sqrt(g), g^ij, Gamma
-    double* J;       // [9][N] current chart Jacobian (FP64)
+    void* J;         // [9][N] current chart Jacobian at the precision R of the arithmetic (FP64 for FP64
+                     // storage, FP32 otherwise)
     void* jf;        // [N] rho u (x, y, z, unused) of every node
     double* face[6]; // [3][face nodes] boundary velocity of non-periodic faces
     long long face_n[6];

@@ -392,16 +392,11 @@ __device__ __forceinline__ void transform_store(const Lat& L, S* __restrict__ Po
     }
 }
 
-// D phi = Jn^-1 Jo at the precision Cm (FP64 for FP64 storage, FP32 otherwise)
+// D phi = Jn^-1 Jo at the precision Cm of n and o (FP64 for FP64 storage,
+// FP32 otherwise)
 template <class Cm, class R>
-__device__ __forceinline__ void dphi(const double (&Jn)[9], const double (&Jo)[9], R (&Dp)[3][3])
+__device__ __forceinline__ void dphi_of(const Cm (&n)[9], const Cm (&o)[9], R (&Dp)[3][3])
 {
-    Cm n[9], o[9];
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        n[k] = to_real<Cm>(Jn[k]);
-        o[k] = to_real<Cm>(Jo[k]);
-    }
     Cm inv[9];
     {
         const Cm c00 = n[4] * n[8] - n[5] * n[7], c01 = n[5] * n[6] - n[3] * n[8], c02 = n[3] * n[7] - n[4] * n[6];
@@ -425,6 +420,19 @@ __device__ __forceinline__ void dphi(const double (&Jn)[9], const double (&Jo)[9
             for (int m = 0; m < 3; m++) s += inv[i * 3 + m] * o[m * 3 + k];
             Dp[i][k] = R(s);
         }
+}
+
+// the same from FP64 Jacobians, rounded to Cm first
+template <class Cm, class R>
+__device__ __forceinline__ void dphi(const double (&Jn)[9], const double (&Jo)[9], R (&Dp)[3][3])
+{
+    Cm n[9], o[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        n[k] = to_real<Cm>(Jn[k]);
+        o[k] = to_real<Cm>(Jo[k]);
+    }
+    dphi_of<Cm, R>(n, o, Dp);
 }
 
 // the f-moments and history of a node in the form the transformation takes:
@@ -460,7 +468,7 @@ template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
                                                    const R* __restrict__ hin, R* __restrict__ hout,
                                                    const R* __restrict__ geo_old, const R* __restrict__ geo_new,
-                                                   double* __restrict__ J, const double* __restrict__ Jnew,
+                                                   R* __restrict__ J, const double* __restrict__ Jnew,
                                                    long long stride, long long v0, long long cnt, int literal)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -470,16 +478,16 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
     node_coords(L, v, x, y, z);
     R in[20];
     transform_inputs<S, R>(L, Pin, hin, geo_old, x, y, z, v, literal, in);
-    // D phi = Jnew^-1 Jold, in FP64 for FP64 storage and in FP32 otherwise
-    // (the FP64 Jacobians rounded; D phi is stored at the precision of R)
-    double Jo[9], Jn[9];
+    // D phi = Jnew^-1 Jold at the precision of R (the stored Jacobian is kept
+    // in R; the caller's FP64 Jnew is rounded to it and becomes the stored one)
+    R Jo[9], Jn[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
         Jo[k] = J[k * L.N + v];
-        Jn[k] = Jnew[k * stride + t];
+        Jn[k] = to_real<R>(Jnew[k * stride + t]);
     }
     R Dp[3][3];
-    dphi<R, R>(Jn, Jo, Dp);
+    dphi_of<R, R>(Jn, Jo, Dp);
 #pragma unroll
     for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
     const R j[3] = {in[1], in[2], in[3]}, B[3] = {in[11], in[12], in[13]};
@@ -497,7 +505,7 @@ template <class S, class R>
 __global__ void __launch_bounds__(TPB, 3) k_chart(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
                                                const R* __restrict__ hin, R* __restrict__ hout,
                                                const R* __restrict__ geo_old, R* __restrict__ geo_new,
-                                               double* __restrict__ J, const double* __restrict__ g6,
+                                               R* __restrict__ J, const double* __restrict__ g6,
                                                const double* __restrict__ dg18, const double* __restrict__ Jnew,
                                                int literal, int* bad)
 {
@@ -512,14 +520,14 @@ __global__ void __launch_bounds__(TPB, 3) k_chart(Lat L, const S* __restrict__ P
     node_coords(L, v, x, y, z);
     R in[20];
     transform_inputs<S, R>(L, Pin, hin, geo_old, x, y, z, v, literal, in);
-    double Jo[9], Jn[9];
+    R Jo[9], Jn[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
         Jo[k] = J[k * L.N + v];
-        Jn[k] = Jnew[k * L.N + v];
+        Jn[k] = to_real<R>(Jnew[k * L.N + v]);
     }
     R Dp[3][3];
-    dphi<R, R>(Jn, Jo, Dp);
+    dphi_of<R, R>(Jn, Jo, Dp);
 #pragma unroll
     for (int k = 0; k < 9; k++) J[k * L.N + v] = Jn[k];
     const R j[3] = {in[1], in[2], in[3]}, B[3] = {in[11], in[12], in[13]};
@@ -564,7 +572,7 @@ __device__ __forceinline__ void interp_axis(double p, int n, bool per, int& i0, 
 // pass 2: every new node from the fields at psi(x~) = psi3[.][v]
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_transform_interp(Lat L, S* __restrict__ Pout, R* __restrict__ hout,
-                                                          const R* __restrict__ geo_new, const double* __restrict__ J,
+                                                          const R* __restrict__ geo_new, const R* __restrict__ J,
                                                           const double* __restrict__ Jnew,
                                                           const double* __restrict__ psi, const R* __restrict__ mf,
                                                           int literal)
@@ -592,7 +600,7 @@ __global__ void __launch_bounds__(TPB) k_transform_interp(Lat L, S* __restrict__
     for (int k = 0; k < 9; k++) {
         double s = 0.0;
 #pragma unroll
-        for (int c = 0; c < 8; c++) s += w[c] * J[k * L.N + ix[c]];
+        for (int c = 0; c < 8; c++) s += w[c] * double(J[k * L.N + ix[c]]);
         Jo[k] = s;
         Jn[k] = Jnew[k * L.N + v];
     }
@@ -617,7 +625,7 @@ __global__ void __launch_bounds__(TPB) k_transform_interp(Lat L, S* __restrict__
 // ---------------------------------------------------------------------------
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_readout(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                 const R* __restrict__ geo, const double* __restrict__ J,
+                                                 const R* __restrict__ geo, const R* __restrict__ J,
                                                  double* __restrict__ rho_out, double* __restrict__ u_out,
                                                  long long stride, long long v0, long long cnt, int cartesian)
 {
@@ -636,7 +644,9 @@ __global__ void __launch_bounds__(TPB) k_readout(Lat L, const S* __restrict__ P,
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             double s = u[a];
-            if (cartesian) s = J[(a * 3 + 0) * L.N + v] * u[0] + J[(a * 3 + 1) * L.N + v] * u[1] + J[(a * 3 + 2) * L.N + v] * u[2];
+            if (cartesian)
+                s = double(J[(a * 3 + 0) * L.N + v]) * u[0] + double(J[(a * 3 + 1) * L.N + v]) * u[1] +
+                    double(J[(a * 3 + 2) * L.N + v]) * u[2];
             u_out[a * stride + t] = s;
         }
     }
@@ -704,7 +714,7 @@ __global__ void __launch_bounds__(TPB) k_mass(Lat L, const S* __restrict__ P, co
 
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_wall_force(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                                    const R* __restrict__ geo, const double* __restrict__ J,
+                                                    const R* __restrict__ geo, const R* __restrict__ J,
                                                     int axis, int side, double* acc)
 {
     // one thread per node of the face
@@ -736,7 +746,7 @@ __global__ void __launch_bounds__(TPB) k_wall_force(Lat L, const S* __restrict__
         for (int a = 0; a < 3; a++) {
             double s = 0.0;
 #pragma unroll
-            for (int i = 0; i < 3; i++) s += J[(a * 3 + i) * L.N + v] * double(Tn[i]);
+            for (int i = 0; i < 3; i++) s += double(J[(a * 3 + i) * L.N + v]) * double(Tn[i]);
             val[a] = sgn * s * double(G.sg);
         }
     }
@@ -745,7 +755,7 @@ __global__ void __launch_bounds__(TPB) k_wall_force(Lat L, const S* __restrict__
 
 template <class S, class R>
 __global__ void __launch_bounds__(TPB) k_check(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
-                                               const R* __restrict__ geo, const double* __restrict__ J, double* acc)
+                                               const R* __restrict__ geo, const R* __restrict__ J, double* acc)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double val[1] = {0.0};
@@ -759,7 +769,8 @@ __global__ void __launch_bounds__(TPB) k_check(Lat L, const S* __restrict__ P, c
         for (int a = 0; a < 3; a++) u[a] = double(M.j[a]) / double(M.rho);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            double va = J[(a * 3) * L.N + v] * u[0] + J[(a * 3 + 1) * L.N + v] * u[1] + J[(a * 3 + 2) * L.N + v] * u[2];
+            double va = double(J[(a * 3) * L.N + v]) * u[0] + double(J[(a * 3 + 1) * L.N + v]) * u[1] +
+                        double(J[(a * 3 + 2) * L.N + v]) * u[2];
             s2 += va * va;
         }
         const bool bad = !(double(M.rho) > 0.0) || !(s2 <= 0.09);  // false for NaN too
@@ -817,13 +828,13 @@ template <class S, class R> struct Launch {
     static void transform(const cslbm_ctx* c, const double* Jnew, long long stride, long long v0, long long cnt)
     {
         k_transform<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc),
-                                                               H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, Jnew,
+                                                               H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), (R*)c->J, Jnew,
                                                                stride, v0, cnt, c->p.transform_flags & 1);
     }
     static void chart_change(const cslbm_ctx* c, const double* g6, const double* dg18, const double* Jnew, int* bad)
     {
         k_chart<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), P(c, 1 - c->pc), H(c, c->hc),
-                                                           H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), c->J, g6,
+                                                           H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), (R*)c->J, g6,
                                                            dg18, Jnew, c->p.transform_flags & 1, bad);
     }
     static void transform_interp(const cslbm_ctx* c, const double* Jnew, const double* psi3, void* scratch)
@@ -832,13 +843,13 @@ template <class S, class R> struct Launch {
         k_moment_fields<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
                                                                    (R*)scratch, lit);
         k_transform_interp<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, 1 - c->pc), H(c, 1 - c->hc),
-                                                                      G(c, 1 - c->gc), c->J, Jnew, psi3,
+                                                                      G(c, 1 - c->gc), (R*)c->J, Jnew, psi3,
                                                                       (const R*)scratch, lit);
     }
     static void readout(const cslbm_ctx* c, double* rho, double* u3, long long stride, long long v0, long long cnt,
                         int cartesian)
     {
-        k_readout<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), c->J,
+        k_readout<S, R><<<nblocks(cnt), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), (const R*)c->J,
                                                              rho, u3, stride, v0, cnt, cartesian);
     }
     static void mass(const cslbm_ctx* c, double* acc)
@@ -850,12 +861,12 @@ template <class S, class R> struct Launch {
         const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
         long long nf = (long long)c->n[a1] * c->n[a2];
         k_wall_force<S, R><<<nblocks(nf), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
-                                                               c->J, axis, side, acc);
+                                                               (const R*)c->J, axis, side, acc);
     }
     static void check(const cslbm_ctx* c, double* acc)
     {
-        k_check<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), c->J,
-                                                            acc);
+        k_check<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                            (const R*)c->J, acc);
     }
     static constexpr cslbm_ops ops()
     {
