@@ -899,7 +899,7 @@ def main():
     ms_per_step = r["ms"] / args.steps
     value = whole_job_mlups(world, N, STEPS_PER_CYCLE * args.steps, r["ms"])
     state_gb = BYTES_PER_NODE[spec["storage"]] * N / 1e9
-    e2e = None if args.no_e2e else end_to_end(args, lat, r["snaps"], N, world)
+    e2e = None if args.no_e2e else end_to_end(args, lat, r["snaps"], N, world, mixed=spec["storage"] != "fp64")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -957,21 +957,27 @@ def main():
         dist.destroy_process_group()
 
 
-def end_to_end(args, lat, snaps, N, world):
+def end_to_end(args, lat, snaps, N, world, mixed=True):
     """The same cycles through the public API with every cycle's inputs
     copied from pinned host buffers: the metric, its derivatives, the
     Jacobian and the face velocities go host -> device on a copy stream into
     one of two device buffers while the previous cycle computes (the next
     cycle's chart change waits for its copy), and the mass and wall force are
     read back every cycle.  All copies and reads are inside the timed
-    region."""
+    region.  With `mixed` (FP32-arithmetic storage) the derivatives and the
+    Jacobian travel in FP32 and the chart change is
+    cslbm_update_metric_mixed, which leaves the same state as the FP64-input
+    call (the library rounds both to FP32 before use): 156 instead of 264
+    bytes per node over a host link of about 210 GB/s."""
     import torch
     keys = ("g6", "dg18", "J9")
+    dtype = {"g6": torch.float64, "dg18": torch.float32 if mixed else torch.float64,
+             "J9": torch.float32 if mixed else torch.float64}
     pinned = []
     for ch, faces in snaps:
         p = {}
         for k in keys:
-            p[k] = torch.empty(getattr(ch, k).shape, dtype=torch.float64, pin_memory=True)
+            p[k] = torch.empty(getattr(ch, k).shape, dtype=dtype[k], pin_memory=True)
             p[k].numpy()[...] = getattr(ch, k)
         p["faces"] = {}
         for key, u in faces.items():
@@ -979,7 +985,8 @@ def end_to_end(args, lat, snaps, N, world):
             t.numpy()[...] = u
             p["faces"][key] = t
         pinned.append(p)
-    h2d = sum(pinned[1][k].numel() * 8 for k in keys) + sum(u.numel() * 8 for u in pinned[1]["faces"].values())
+    h2d = sum(pinned[1][k].numel() * pinned[1][k].element_size() for k in keys) + \
+        sum(u.numel() * 8 for u in pinned[1]["faces"].values())
     d2h = 4 * 8
     dev = [{k: torch.empty_like(pinned[1][k], device="cuda") for k in keys} for _ in range(2)]
     for d in dev:
@@ -1008,7 +1015,10 @@ def end_to_end(args, lat, snaps, N, world):
                 upload(k + 1, 1 - slot)
             lat.stream.wait_event(ready[slot])
             d = dev[slot]
-            lat.update_metric(d["g6"], d["dg18"], d["J9"])
+            if mixed:
+                lat.update_metric_mixed(d["g6"], d["dg18"], d["J9"])
+            else:
+                lat.update_metric(d["g6"], d["dg18"], d["J9"])
             for (a, s), u in d["faces"].items():
                 lat.set_boundary_velocity(a, s, u)
             free[slot].record(lat.stream)
@@ -1027,7 +1037,8 @@ def end_to_end(args, lat, snaps, N, world):
     return {"value": world * N * STEPS_PER_CYCLE * args.steps / t_e2e / 1e6, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "note": "inputs copied host -> device on a second stream, double-buffered, overlapping the previous "
-                    "cycle's steps"}
+                    "cycle's steps" + ("; metric FP64, its derivatives and the Jacobian FP32 "
+                                       "(cslbm_update_metric_mixed, the same state as FP64 inputs)" if mixed else "")}
 
 
 if __name__ == "__main__":

@@ -128,6 +128,19 @@ cslbm_status cslbm_set_jacobian(cslbm_ctx* ctx, const double* J9, int on_device)
 cslbm_status cslbm_update_metric(cslbm_ctx* ctx, const double* g6, const double* dg18,
                                  const double* Jnew9, int on_device);
 
+/* cslbm_update_metric with the metric derivatives dg18 [18][N] and the new
+ * Jacobian Jnew9 [9][N] in FP32, the metric g6 [6][N] still in FP64 (its
+ * inversion is FP64).  For FP32, FP16 and BF16 storage the library rounds
+ * dg and J to FP32 before any use (Gamma and D phi are formed in FP32), so
+ * the state this call leaves is bit for bit the one cslbm_update_metric
+ * leaves with the same values in FP64; it lets a caller that uploads the
+ * chart every few steps move 156 instead of 264 bytes per node.  Every array
+ * is device memory owned by the caller and read before the call's work on
+ * the context's stream ends.  EINVAL for FP64 storage, a null or host
+ * pointer; ESTATE before cslbm_init_equilibrium; det g <= 0 as for
+ * cslbm_update_metric (reported by the next cslbm_check). */
+cslbm_status cslbm_update_metric_mixed(cslbm_ctx* ctx, const double* g6, const float* dg18, const float* Jnew9);
+
 /* Initial state f = f^eq(rho, u; g) (App. B) with the boundary rule on the
  * boundary nodes, and forcing history F(x,-dt) := F(x,0).  rho [N] and
  * u3 [3][N] (contravariant) are FP64; NULL selects rho = 1 / u = 0. */

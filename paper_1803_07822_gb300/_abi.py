@@ -51,6 +51,7 @@ SIGNATURES = {
     "cslbm_set_metric": [_P, _P, _P, _I],
     "cslbm_set_jacobian": [_P, _P, _I],
     "cslbm_update_metric": [_P, _P, _P, _P, _I],
+    "cslbm_update_metric_mixed": [_P, _P, _P, _P],
     "cslbm_init_equilibrium": [_P, _P, _P, _I],
     "cslbm_set_boundary_velocity": [_P, _I, _I, _P, _I],
     "cslbm_step": [_P, _I],

@@ -455,6 +455,25 @@ cslbm_status cslbm_update_metric(cslbm_ctx* c, const double* g6, const double* d
     return CSLBM_OK;
 }
 
+cslbm_status cslbm_update_metric_mixed(cslbm_ctx* c, const double* g6, const float* dg18, const float* Jnew9)
+{
+    if (!c || !g6 || !dg18 || !Jnew9) return fail(CSLBM_EINVAL, "null argument");
+    if (c->r_bytes == 8) return fail(CSLBM_EINVAL, "FP64 storage takes its derivatives and Jacobian in FP64");
+    for (const void* q : {(const void*)g6, (const void*)dg18, (const void*)Jnew9})
+        if (!is_device_memory(q)) return fail(CSLBM_EINVAL, "every array of update_metric_mixed is device memory");
+    if (!c->has_state) return fail(CSLBM_ESTATE, "update_metric before init_equilibrium");
+    int* bad = (int*)(c->scratch + 32);
+    if (!c->metric_check_pending) CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    c->ops->chart_change_mixed(c, g6, dg18, Jnew9, bad);
+    c->launches++;
+    LAUNCH_CHECK("chart-change kernel");
+    c->metric_check_pending = 1;
+    c->pc ^= 1;
+    c->hc ^= 1;
+    c->gc ^= 1;
+    return CSLBM_OK;
+}
+
 cslbm_status cslbm_init_equilibrium(cslbm_ctx* c, const double* rho, const double* u3, int on_device)
 {
     if (!c) return fail(CSLBM_EINVAL, "ctx is null");

@@ -97,6 +97,7 @@ struct cslbm_ops {
     // node): G[1-gc] from g6/dg18, then P[pc],H[hc] -> P[1-pc],H[1-hc] and J
     // replaced by Jnew; *bad set non-zero on det g <= 0
     void (*chart_change)(const cslbm_ctx*, const double* g6, const double* dg18, const double* Jnew, int* bad);
+    void (*chart_change_mixed)(const cslbm_ctx*, const double* g6, const float* dg18, const float* Jnew, int* bad);
     // chart change with interpolation: the transformation inputs of every node
     // into scratch [20][N] (precision R), then every node of P[1-pc],H[1-hc]
     // from them at psi3 [3][N] (old lattice coordinates) with G[1-gc]; J (old)

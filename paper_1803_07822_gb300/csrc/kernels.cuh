@@ -34,11 +34,13 @@ __device__ __forceinline__ void node_coords(const Lat& L, long long v, int& x, i
 template <class R> __device__ __forceinline__ R to_real(double x);
 template <> __device__ __forceinline__ float to_real<float>(double x) { return f64_to_f32_rn(x); }
 template <> __device__ __forceinline__ double to_real<double>(double x) { return x; }
+// FP32 inputs (the mixed-precision chart change) are taken as they are
+template <class R> __device__ __forceinline__ R to_real(float x) { return R(x); }
 
 // geometry of node v (G[.][v]: sqrt(g), g^ij, Gamma) from its metric g6 /
 // dg18 at entry t of the inputs (stride apart); returns false for det g <= 0
-template <class R>
-__device__ __forceinline__ bool metric_node(const double* __restrict__ g6, const double* __restrict__ dg18,
+template <class R, class DT = double>
+__device__ __forceinline__ bool metric_node(const double* __restrict__ g6, const DT* __restrict__ dg18,
                                             long long stride, long long t, R* __restrict__ geo, long long N,
                                             long long v, R& sg_out)
 {
@@ -501,18 +503,18 @@ __global__ void __launch_bounds__(TPB) k_transform(Lat L, const S* __restrict__ 
 // transformation of its state (as k_transform) with the new sqrt(g) from
 // registers.  The metric's FP64 arithmetic overlaps the transformation's
 // memory traffic instead of running as a pass of its own.
-template <class S, class R>
+template <class S, class R, class DT = double>
 __global__ void __launch_bounds__(TPB, 3) k_chart(Lat L, const S* __restrict__ Pin, S* __restrict__ Pout,
                                                const R* __restrict__ hin, R* __restrict__ hout,
                                                const R* __restrict__ geo_old, R* __restrict__ geo_new,
                                                R* __restrict__ J, const double* __restrict__ g6,
-                                               const double* __restrict__ dg18, const double* __restrict__ Jnew,
+                                               const DT* __restrict__ dg18, const DT* __restrict__ Jnew,
                                                int literal, int* bad)
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= L.N) return;
     R sgn;
-    if (!metric_node<R>(g6, dg18, L.N, v, geo_new, L.N, v, sgn)) {
+    if (!metric_node<R, DT>(g6, dg18, L.N, v, geo_new, L.N, v, sgn)) {
         atomicOr(bad, 1);
         return;
     }
@@ -837,6 +839,17 @@ template <class S, class R> struct Launch {
                                                            H(c, 1 - c->hc), G(c, c->gc), G(c, 1 - c->gc), (R*)c->J, g6,
                                                            dg18, Jnew, c->p.transform_flags & 1, bad);
     }
+    // the same with the derivatives and the Jacobian in FP32 (FP32-arithmetic
+    // storage only: there they are rounded to FP32 before any use)
+    static void chart_change_mixed(const cslbm_ctx* c, const double* g6, const float* dg18, const float* Jnew,
+                                   int* bad)
+    {
+        if constexpr (!std::is_same<R, double>::value)
+            k_chart<S, R, float><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), P(c, 1 - c->pc),
+                                                                      H(c, c->hc), H(c, 1 - c->hc), G(c, c->gc),
+                                                                      G(c, 1 - c->gc), (R*)c->J, g6, dg18, Jnew,
+                                                                      c->p.transform_flags & 1, bad);
+    }
     static void transform_interp(const cslbm_ctx* c, const double* Jnew, const double* psi3, void* scratch)
     {
         const int lit = c->p.transform_flags & 1;
@@ -870,8 +883,9 @@ template <class S, class R> struct Launch {
     }
     static constexpr cslbm_ops ops()
     {
-        return cslbm_ops{&metric, &init_scatter, &momentum_field, &step, &half_shift,
-                         &transform, &chart_change, &transform_interp, &readout, &mass, &wall_force, &check};
+        return cslbm_ops{&metric,    &init_scatter,       &momentum_field,   &step,    &half_shift, &transform,
+                         &chart_change, &chart_change_mixed, &transform_interp, &readout, &mass,       &wall_force,
+                         &check};
     }
 };
 

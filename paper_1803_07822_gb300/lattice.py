@@ -100,6 +100,20 @@ class CurvedLattice:
             raise ValueError("metric inputs must all be host or all device arrays")
         call("cslbm_update_metric", self.ctx, p1, p2, p3, d1)
 
+    def update_metric_mixed(self, g6, dg18, J9):
+        """update_metric with the derivatives and the Jacobian as FP32 CUDA
+        tensors (the metric stays FP64): the same state for FP32-arithmetic
+        storage, 156 instead of 264 bytes per node to upload."""
+        torch = _torch()
+        g = g6.detach().to(self.device, torch.float64).contiguous()
+        d = dg18.detach().to(self.device, torch.float32).contiguous()
+        J = J9.detach().to(self.device, torch.float32).contiguous()
+        for t, rows in ((g, 6), (d, 18), (J, 9)):
+            if t.numel() != rows * self.N:
+                raise ValueError(f"expected {rows * self.N} values, got {t.numel()}")
+        call("cslbm_update_metric_mixed", self.ctx, g.data_ptr(), d.data_ptr(), J.data_ptr())
+        self._hold(g, d, J)
+
     def update_metric_interp(self, g6, dg18, J9, psi3):
         """Chart change with interpolation: every new node takes the old
         state's moments at psi3 [3, N] (old lattice coordinates of its point)."""
