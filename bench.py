@@ -686,7 +686,7 @@ def transform_interp_report(lat, dev, layout, reps=5):
         out[mode] = e0.elapsed_time(e1) / (reps * len(pairs))
     return {"node_wise_ms": out["node"], "interp_ms": out["interp"], "nodes": lat.N,
             "note": "one chart change incl. the metric kernel; the interpolating form adds the moment-field pass "
-                    "and reads 8 corners per node (20 fields + the FP64 Jacobian)"}
+                    "and reads 8 corners per node (20 fields + the Jacobian)"}
 
 
 def oracle_gradient_sample(spec, order=4):
