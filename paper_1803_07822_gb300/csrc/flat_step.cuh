@@ -136,6 +136,25 @@ __device__ __forceinline__ void site_axis(int r, int n, bool per_lo, bool per_hi
 template <class R>
 __device__ __forceinline__ Mom4<R> mom_site(const Lat& L, const Mom4<R>* __restrict__ jf, int x, int y, int z)
 {
+    // most sites of a face node's stencil are lattice nodes (after a periodic
+    // wrap): one load, the value the weighted sum below would give
+    {
+        const int r[3] = {x, y, z};
+        int w[3];
+        bool ghost = false;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            w[a] = r[a];
+            if (r[a] < 0) {
+                if (L.bclo[a] == BC_PERIODIC) w[a] += L.n[a];
+                else ghost = true;
+            } else if (r[a] >= L.n[a]) {
+                if (L.bchi[a] == BC_PERIODIC) w[a] -= L.n[a];
+                else ghost = true;
+            }
+        }
+        if (!ghost) return jf[((unsigned)w[2] * L.n[1] + w[1]) * (unsigned)L.n[0] + w[0]];
+    }
     int x0, x1, y0, y1, z0, z1;
     float wx0, wx1, wy0, wy1, wz0, wz1;
     site_axis(x, L.n[0], L.bclo[0] == BC_PERIODIC, L.bchi[0] == BC_PERIODIC, x0, x1, wx0, wx1);
