@@ -689,27 +689,36 @@ __device__ __noinline__ R face_rho(const Lat& L, const S* __restrict__ P, const 
     return M.rho;
 }
 
+// a value of the arithmetic's type as FP64, exactly (FP32 through the integer
+// units: a conversion on the FP64 pipe costs as much as the product)
+__device__ __forceinline__ double exact64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double exact64(double v) { return v; }
+
+// Total mass: every thread sums sqrt(g) rho of the nodes v = i, i + stride, ...
+// in FP64 (the product of two FP32 values is exact in FP64), then one block
+// reduction; a grid of the resident blocks keeps the FP64 work per node at
+// one multiply and one add.
 template <class S, class R>
-__global__ void __launch_bounds__(TPB) k_mass(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
+__global__ void __launch_bounds__(TPB, 3) k_mass(Lat L, const S* __restrict__ P, const R* __restrict__ hist,
                                               const R* __restrict__ geo, double* acc)
 {
-    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double val[1] = {0.0};
-    if (v < L.N) {
-        int x, y, z;
-        node_coords(L, v, x, y, z);
+    const unsigned N = (unsigned)L.N, n0 = L.n[0], n1 = L.n[1];
+    for (unsigned v = blockIdx.x * TPB + threadIdx.x; v < N; v += gridDim.x * TPB) {
+        const unsigned row = v / n0, z = row / n1;
+        const int x = (int)(v - row * n0), y = (int)(row - z * n1);
         const R sg = geo[v];
         R rho;
-        if (on_boundary(L, x, y, z)) {
-            rho = face_rho<S, R>(L, P, hist, geo, x, y, z, v, sg);
+        if (on_boundary(L, x, y, (int)z)) {
+            rho = face_rho<S, R>(L, P, hist, geo, x, y, (int)z, v, sg);
         } else {
             // rho = sqrt(g)(1 + sum s) + A/2 of the pulled populations (the same sums as node_moments)
             R s[Q], m0, m1[3], m2[6];
-            gather_raw<S, R>(L, P, x, y, z, s);
+            gather_raw<S, R>(L, P, x, y, (int)z, s);
             sums(s, m0, m1, m2);
             rho = sg * (R(1) + m0) + R(0.5) * hist[v];
         }
-        val[0] = double(sg) * double(rho);
+        val[0] += exact64(sg) * exact64(rho);
     }
     block_reduce_add<1>(val, acc);
 }
@@ -867,7 +876,10 @@ template <class S, class R> struct Launch {
     }
     static void mass(const cslbm_ctx* c, double* acc)
     {
-        k_mass<S, R><<<nblocks(c->N), TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc), acc);
+        // resident blocks of TPB threads: three per SM at the kernel's register bound
+        const unsigned nb = nblocks(c->N), res = 3u * (unsigned)c->n_sm;
+        k_mass<S, R><<<nb < res ? nb : res, TPB, 0, c->stream>>>(make_lat(c), P(c, c->pc), H(c, c->hc), G(c, c->gc),
+                                                                acc);
     }
     static void wall_force(const cslbm_ctx* c, int axis, int side, double* acc)
     {
