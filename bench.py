@@ -663,6 +663,9 @@ def transform_interp_report(lat, dev, layout, reps=5):
     import torch
     w = layout[0]
     grid = torch.as_tensor(np.stack(I.grid(lat.n)), device="cuda")
+    # both forms with FP64 inputs (the interpolating call takes no other),
+    # converted once outside the timed region
+    dev = [{k: (v.double() if k in ("g6", "dg18", "J9") else v) for k, v in d.items()} for d in dev]
     pairs = [(dev[i], dev[i + 1]) for i in range(len(dev) - 1)]
     psis = []
     for a, b in pairs:
@@ -777,7 +780,10 @@ def channel_cycles(spec, args, rank, world, local, steps):
     cycled, each cycle a chart change with transformation, 10 LBM steps and
     the mass and wall-force reductions.  Device time with CUDA events on the
     library's stream, the slowest rank's; one LBM step timed by the library
-    (profiling on) for the roofline."""
+    (profiling on) for the roofline.  For FP32-arithmetic storage the chart
+    change takes its derivatives and Jacobian in FP32
+    (cslbm_update_metric_mixed: the library rounds them to FP32 before use,
+    so the state is the one FP64 inputs give, bit for bit)."""
     import torch
 
     from paper_1803_07822_gb300.lattice import CurvedLattice
@@ -789,9 +795,12 @@ def channel_cycles(spec, args, rank, world, local, steps):
     lat = CurvedLattice(spec["n"], w["bc_lo"], w["bc_hi"], tau=w["tau"], fext=w["fext"], storage=spec["storage"],
                         step_kernel=args.step_kernel)
     # device-resident inputs for the kernel-throughput run
+    mixed = spec["storage"] != "fp64"
     dev = []
     for ch, faces in snaps:
         d = {k: torch.as_tensor(getattr(ch, k), device="cuda") for k in ("g6", "dg18", "J9")}
+        if mixed:
+            d["dg18"], d["J9"] = d["dg18"].float(), d["J9"].float()
         d["faces"] = {key: torch.as_tensor(u, device="cuda") for key, u in faces.items()}
         dev.append(d)
     ch0, faces0 = snaps[0]
@@ -802,7 +811,10 @@ def channel_cycles(spec, args, rank, world, local, steps):
 
     def cycle_dev(k):
         d = dev[1 + k % args.snapshots]
-        lat.update_metric(d["g6"], d["dg18"], d["J9"])
+        if mixed:
+            lat.update_metric_mixed(d["g6"], d["dg18"], d["J9"])
+        else:
+            lat.update_metric(d["g6"], d["dg18"], d["J9"])
         for (a, s), u in d["faces"].items():
             lat.set_boundary_velocity(a, s, u)
         lat.step(STEPS_PER_CYCLE)
@@ -906,6 +918,8 @@ def main():
         "vs_baseline": None, "dtype": "f32" if spec["storage"] == "fp32" else spec["storage"], "data": "synthetic",
         "config": {"workload": spec["label"], "nodes": N, "lbm_steps_per_step": STEPS_PER_CYCLE,
                    "l2": f"inputs > L2 ({state_gb:.1f} GB of state per LBM step), no flush",
+                   "chart_inputs": ("g FP64, dg and J FP32 (cslbm_update_metric_mixed: the state of FP64 inputs, "
+                                    "bit for bit)" if spec["storage"] != "fp64" else "g, dg, J FP64"),
                    "state_finite_after_run": r["ok"]},
         "roofline": roofline_of(spec, args, N, r["step_ms"]),
         "e2e": e2e,
