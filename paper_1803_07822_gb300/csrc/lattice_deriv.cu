@@ -118,22 +118,36 @@ __device__ __forceinline__ long long nb_index(const Box& B, int x, int y, int z)
 __global__ void __launch_bounds__(TBL) k_pad(const __grid_constant__ Box B, const double* __restrict__ f, int order,
                                              double* __restrict__ F)
 {
-    const long long s = blockIdx.x * (long long)TBL + threadIdx.x;
-    if (s >= B.Ne) return;
+    // 32-bit site arithmetic (the padded lattice has fewer than 2^32 sites)
+    const unsigned s = blockIdx.x * TBL + threadIdx.x;
+    if (s >= (unsigned)B.Ne) return;
     const double* fc = f + (long long)blockIdx.y * B.N;
-    const long long row = s / B.ne[0];
-    const int x = (int)(s - row * B.ne[0]) - B.pad[0];
-    const int y = (int)(row % B.ne[1]) - B.pad[1];
-    const int z = (int)(row / B.ne[1]) - B.pad[2];
+    const unsigned ne0 = B.ne[0], ne1 = B.ne[1], row = s / ne0, zr = row / ne1;
+    const int x = (int)(s - row * ne0) - B.pad[0];
+    const int y = (int)(row - zr * ne1) - B.pad[1];
+    const int z = (int)zr - B.pad[2];
     // with sum_{l>0} w_l = 2/3, w = 1/18 on the six faces, 1/36 on the twelve
     // edges: F = (5/3) f0 - (S_faces + S_edges / 2) / 18
     double f0, sf = 0.0, se = 0.0;
     if (inner(B, 0, x) && inner(B, 1, y) && inner(B, 2, z)) {
-        f0 = __ldg(fc + ((long long)z * B.n[1] + y) * B.n[0] + x);
+        // neighbour offsets per axis, wrapped on periodic axes (as nb_index)
+        const unsigned n0 = B.n[0], n01 = n0 * (unsigned)B.n[1];
+        unsigned o[3][3];
+        const int r[3] = {x, y, z};
+        const unsigned st[3] = {1u, n0, n01};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int c = -1; c <= 1; c++) {
+                int q = r[a] + c;
+                wrap(B, a, q);
+                o[a][c + 1] = (unsigned)q * st[a];
+            }
+        f0 = __ldg(fc + (o[2][1] + o[1][1] + o[0][1]));
         if (order == 4) {
 #pragma unroll
             for (int l = 1; l < Q; l++) {
-                const double fl = __ldg(fc + nb_index(B, x + cvec(l, 0), y + cvec(l, 1), z + cvec(l, 2)));
+                const double fl = __ldg(fc + (o[2][cvec(l, 2) + 1] + o[1][cvec(l, 1) + 1] + o[0][cvec(l, 0) + 1]));
                 if (l <= 6) sf += fl;
                 else se += fl;
             }
@@ -167,17 +181,32 @@ __device__ __forceinline__ long long pad_index(const Box& B, int x, int y, int z
 __global__ void __launch_bounds__(TBL) k_grad(const __grid_constant__ Box B, int ncomp, const double* __restrict__ F,
                                               double* __restrict__ out)
 {
-    const long long v = blockIdx.x * (long long)TBL + threadIdx.x;
-    if (v >= B.N) return;
+    const unsigned v = blockIdx.x * TBL + threadIdx.x;
+    if (v >= (unsigned)B.N) return;
     const int c = blockIdx.y;
     const double* Fc = F + (long long)c * B.Ne;
-    const long long row = v / B.n[0];
-    const int x = (int)(v - row * B.n[0]), y = (int)(row % B.n[1]), z = (int)(row / B.n[1]);
+    const unsigned n0 = B.n[0], n1 = B.n[1], row = v / n0, zr = row / n1;
+    const int x = (int)(v - row * n0), y = (int)(row - zr * n1), z = (int)zr;
+    // offsets of the sites r + c per axis in the padded lattice (as pad_index)
+    unsigned o[3][3];
+    {
+        const int r[3] = {x, y, z};
+        const unsigned st[3] = {1u, (unsigned)B.ne[0], (unsigned)B.ne[0] * (unsigned)B.ne[1]};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int cc = -1; cc <= 1; cc++) {
+                int q = r[a] + cc;
+                wrap(B, a, q);
+                o[a][cc + 1] = (unsigned)(q + B.pad[a]) * st[a];
+            }
+    }
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
         const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-        const double d = __ldg(Fc + pad_index(B, x + cx, y + cy, z + cz)) - __ldg(Fc + pad_index(B, x - cx, y - cy, z - cz));
+        const double d = __ldg(Fc + (o[2][cz + 1] + o[1][cy + 1] + o[0][cx + 1])) -
+                         __ldg(Fc + (o[2][1 - cz] + o[1][1 - cy] + o[0][1 - cx]));
         const double wd = wq(l) / kCs2;
         if (cx) g0 = fma(cx * wd, d, g0);
         if (cy) g1 = fma(cy * wd, d, g1);
