@@ -48,13 +48,13 @@ template <class R> struct Bufs {
 
 template <class R> __device__ __forceinline__ void add(R* p, R v) { atomicAdd(p, v); }
 
+// (32-bit arithmetic: a context holds fewer than 2^32 nodes)
 __device__ __forceinline__ void node_xyz(const Lat& L, long long v, int& x, int& y, int& z)
 {
-    const long long n01 = (long long)L.n[0] * L.n[1];
-    z = (int)(v / n01);
-    const long long r = v - z * n01;
-    y = (int)(r / L.n[0]);
-    x = (int)(r - (long long)y * L.n[0]);
+    const unsigned vu = (unsigned)v, n0 = L.n[0], n1 = L.n[1], row = vu / n0, zr = row / n1;
+    x = (int)(vu - row * n0);
+    y = (int)(row - zr * n1);
+    z = (int)zr;
 }
 
 // ghost extrapolation of a stencil site reversed: the adjoint lj of the
@@ -79,6 +79,24 @@ __device__ __noinline__ void site_reverse(const Lat& L, int x, int y, int z, R l
             }
 }
 
+// the forward inputs of a face node (boundary rule, ghost stencil), out of
+// line so that the interior path keeps its registers
+template <class R>
+__device__ __noinline__ void face_inputs(const Lat& L, const R* __restrict__ P, const R* __restrict__ H,
+                                         const R* __restrict__ geo, const Mom4<R>* __restrict__ jf, int x, int y,
+                                         int z, R* s, R* d)
+{
+    boundary_pops<R, R>(L, P, H, geo, x, y, z, s);
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
+        const Mom4<R> p = mom_site(L, jf, x + cx, y + cy, z + cz), m = mom_site(L, jf, x - cx, y - cy, z - cz);
+        d[3 * k + 0] = p.x - m.x;
+        d[3 * k + 1] = p.y - m.y;
+        d[3 * k + 2] = p.z - m.z;
+    }
+}
+
 // pass A
 template <class R>
 __global__ void __launch_bounds__(TB_A, 4) k_adj_local(Lat L, const R* __restrict__ P, const R* __restrict__ H,
@@ -86,31 +104,31 @@ __global__ void __launch_bounds__(TB_A, 4) k_adj_local(Lat L, const R* __restric
                                                      const R* __restrict__ lPo, const R* __restrict__ lHo,
                                                      Bufs<R> B, R* __restrict__ lHi)
 {
-    const long long v = blockIdx.x * (long long)TB_A + threadIdx.x;
-    if (v >= L.N) return;
-    const long long N = L.N;
-    int x, y, z;
-    node_xyz(L, v, x, y, z);
+    // 32-bit node arithmetic (a context holds fewer than 2^32 nodes)
+    const unsigned vu = blockIdx.x * TB_A + threadIdx.x;
+    if (vu >= (unsigned)L.N) return;
+    const long long v = vu, N = L.N;
+    const unsigned n0 = L.n[0], n1 = L.n[1], row = vu / n0, zr = row / n1;
+    const int x = (int)(vu - row * n0), y = (int)(row - zr * n1), z = (int)zr;
     const bool face = on_boundary(L, x, y, z);
     R s[Q];
     R d[9][3];
     if (face) {
-        boundary_pops<R, R>(L, P, H, geo, x, y, z, s);
+        R sf[Q], df[27];
+        face_inputs<R>(L, P, H, geo, jf, x, y, z, sf, df);
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-            const Mom4<R> p = mom_site(L, jf, x + cx, y + cy, z + cz), m = mom_site(L, jf, x - cx, y - cy, z - cz);
-            d[k][0] = p.x - m.x;
-            d[k][1] = p.y - m.y;
-            d[k][2] = p.z - m.z;
-        }
+        for (int l = 0; l < Q; l++) s[l] = sf[l];
+#pragma unroll
+        for (int k = 0; k < 9; k++)
+#pragma unroll
+            for (int i = 0; i < 3; i++) d[k][i] = df[3 * k + i];
     } else {
         gather_raw<R, R>(L, P, x, y, z, s);
+        const Nbr nb = nbr_index(L, x, y, z, +1);  // sites x + c, wrapped
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             const int l = 2 * k + 1, cx = cvec(l, 0), cy = cvec(l, 1), cz = cvec(l, 2);
-            const Mom4<R> p = jf[nidx(L, wrapc(x + cx, L.n[0]), wrapc(y + cy, L.n[1]), wrapc(z + cz, L.n[2]))];
-            const Mom4<R> m = jf[nidx(L, wrapc(x - cx, L.n[0]), wrapc(y - cy, L.n[1]), wrapc(z - cz, L.n[2]))];
+            const Mom4<R> p = jf[nbr_off(nb, cx, cy, cz)], m = jf[nbr_off(nb, -cx, -cy, -cz)];
             d[k][0] = p.x - m.x;
             d[k][1] = p.y - m.y;
             d[k][2] = p.z - m.z;
