@@ -237,6 +237,7 @@ def test_host_and_device_inputs_agree_and_state_roundtrip():
 TILED = [
     ("ragged last tile", (20, 29, 13), (2, 0, 1), "inout"),
     ("one row per tile", (256, 24, 12), (2, 0, 1), "inout"),
+    ("one row per tile, periodic flow", (256, 16, 10), (2, 0, 1), "periodic"),
     ("rows straddle warps", (100, 24, 10), (2, 0, 1), "periodic"),
     ("span-x two tiles", (64, 16, 9), (2, 0, 1), "inout"),
     ("walls across x", (32, 16, 40), (0, 1, 2), "inout"),
