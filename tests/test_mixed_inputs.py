@@ -21,7 +21,7 @@ def lattice(w, storage):
     return g
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
 def test_mixed_chart_change_is_bitwise_the_fp64_one(storage):
     import torch
     w = I.dynamic_channel(n=(9, 45, 17), seed=2000, n_modes=6, amp=0.06, tau=0.6, re=20.0, period=400.0, kmax=2,
