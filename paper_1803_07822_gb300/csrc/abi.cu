@@ -234,7 +234,9 @@ void rows_prepare(cslbm_ctx* c)
     if (c->p.step_kernel == CSLBM_STEP_FLAT || c->p.storage == CSLBM_FP64) return;
     int max_smem = 0;
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) return;
-    if (!cslbm::rows::make_plan(c->n, c->p.bc_lo[2] == CSLBM_PERIODIC, (int)c->s_bytes, max_smem, R.plan)) return;
+    if (!cslbm::rows::make_plan(c->n, c->p.bc_lo[1] == CSLBM_PERIODIC, c->p.bc_lo[2] == CSLBM_PERIODIC,
+                                (int)c->s_bytes, max_smem, R.plan))
+        return;
     typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

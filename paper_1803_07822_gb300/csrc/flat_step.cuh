@@ -286,11 +286,23 @@ __device__ __forceinline__ void step_boundary_body(const Lat& L, const S* __rest
                                                    int y, int z)
 {
     const unsigned N = (unsigned)L.N, v = (unsigned)nidx(L, x, y, z);
-    R s[Q];
-    boundary_pops<S, R>(L, Pin, hin, geo, x, y, z, s);
     GeoT<R> G;
     HistT<R> Hp;
     load_geo_hist(geo, hin, v, N, G, Hp);
+    // the boundary rule with the node's own metric and history as loaded
+    Geo<R> Gw;
+    Gw.sg = G.sg;
+    Gw.isg = G.isg;
+#pragma unroll
+    for (int a = 0; a < 6; a++) Gw.gi[a] = G.gi[a];
+    Hist<R> Hw;
+    Hw.A = Hp.A;
+#pragma unroll
+    for (int a = 0; a < 3; a++) Hw.B[a] = Hp.B[a];
+#pragma unroll
+    for (int a = 0; a < 6; a++) Hw.C[a] = Hp.C[a];
+    R s[Q];
+    boundary_pops_w<S, R>(L, Pin, hin, geo, x, y, z, Gw, Hw, s);
     R d[9][3];
 #pragma unroll
     for (int k = 0; k < 9; k++) {

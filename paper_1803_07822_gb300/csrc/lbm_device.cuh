@@ -351,25 +351,36 @@ __device__ __forceinline__ void face_velocity(const Lat& L, int axis, int side, 
 // its inner node (boundary_rule), everything gathered from global memory.
 // Kept out of line where it matters (see boundary_site): it runs for the few
 // nodes on the faces.
+// (the node's own metric and history Gw, Hw supplied by the caller)
 template <class S, class R>
-__device__ __forceinline__ void boundary_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
-                                           const R* __restrict__ geo, int x, int y, int z, R s[Q])
+__device__ __forceinline__ void boundary_pops_w(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                                const R* __restrict__ geo, int x, int y, int z, const Geo<R>& Gw,
+                                                const Hist<R>& Hw, R s[Q])
 {
     int r[3] = {x, y, z}, in[3], axis = 0, side = 0;
     const int bc = classify(L, r, axis, side, in);
     const long long N = L.N;
-    const long long vw = nidx(L, x, y, z), vi = nidx(L, in[0], in[1], in[2]);
+    const long long vi = nidx(L, in[0], in[1], in[2]);
     R si[Q];
     gather_raw<S, R>(L, P, in[0], in[1], in[2], si);
-    Geo<R> Gi, Gw;
+    Geo<R> Gi;
     load_metric(geo, N, vi, Gi);
-    load_metric(geo, N, vw, Gw);
-    Hist<R> Hi, Hw;
+    Hist<R> Hi;
     load_hist(hist, N, vi, Hi);
-    load_hist(hist, N, vw, Hw);
     R uw[3];
     face_velocity(L, axis, side, r, uw);
     boundary_rule(L, bc, si, Gi, Hi, Gw, Hw, uw, s);
+}
+template <class S, class R>
+__device__ __forceinline__ void boundary_pops(const Lat& L, const S* __restrict__ P, const R* __restrict__ hist,
+                                           const R* __restrict__ geo, int x, int y, int z, R s[Q])
+{
+    const long long N = L.N, vw = nidx(L, x, y, z);
+    Geo<R> Gw;
+    load_metric(geo, N, vw, Gw);
+    Hist<R> Hw;
+    load_hist(hist, N, vw, Hw);
+    boundary_pops_w<S, R>(L, P, hist, geo, x, y, z, Gw, Hw, s);
 }
 
 // Node state: shifted populations s = h - w of any node (boundary nodes

@@ -228,7 +228,7 @@ __device__ __forceinline__ void issue_tile(const Lat& L, const Plan& pl, const C
 {
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
     const unsigned N = (unsigned)L.N;
-    const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
+    const int zt = t / pl.nyb, y0 = pl.y1 + (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
     const int TRe = min(pl.TR, n1 - y0);
     const bool yper = L.bclo[1] == BC_PERIODIC, zper = L.bclo[2] == BC_PERIODIC;
     const unsigned v0 = ((unsigned)z * n1 + y0) * n0;
@@ -321,7 +321,7 @@ __device__ __forceinline__ void step_tile(const Lat& L, const Plan& pl, const un
     const int qb = r * n0, q0 = qb + x, qm = qb + xm, qp = qb + xp;
     const bool xface = L.bclo[0] != BC_PERIODIC && (x == 0 || x == n0 - 1);
     const bool yper = L.bclo[1] == BC_PERIODIC;
-    const int zt = t / pl.nyb, y0 = (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
+    const int zt = t / pl.nyb, y0 = pl.y1 + (t - zt * pl.nyb) * pl.TR, z = pl.z0 + zt;
     const int y = y0 + r;
     // nodes on a face are stepped by k_step_faces
     const bool active = r < pl.TR && y < n1 && !(xface || (!yper && (y == 0 || y == n1 - 1)));

@@ -19,6 +19,8 @@ constexpr unsigned long long kWaitNs = 500000000ull;
 struct Plan {
     int TR;        // rows per tile
     int nyb;       // tiles per plane
+    int y1;        // first row of the first tile: 1 when tiles are single rows and axis 1 is
+                   // not periodic (the face rows, stepped by the face pass, get no tile)
     int z0;        // first plane that is not a face plane
     int ntiles;    // nyb * (planes that are not face planes)
     int JS;        // nodes per rho u layer: (TR + 2) n0 rounded up to 8
@@ -33,13 +35,15 @@ inline unsigned smem_bytes(const Plan& pl) { return STAGES * pl.stage_bytes + 2 
 // false when the pass does not apply: rows longer than NT nodes or not a
 // whole number of 16-byte chunks, fewer than NT nodes in all, or stages that
 // do not fit in max_smem bytes
-inline bool make_plan(const int n[3], bool zper, int s_bytes, int max_smem, Plan& pl)
+inline bool make_plan(const int n[3], bool yper, bool zper, int s_bytes, int max_smem, Plan& pl)
 {
     const long long N = (long long)n[0] * n[1] * n[2];
     if (n[0] > NT || n[0] % 4 != 0 || (n[0] * s_bytes) % 16 != 0 || N < NT) return false;
     if (!zper && n[2] < 3) return false;
+    if (!yper && n[1] < 3) return false;
     pl.TR = NT / n[0] < n[1] ? NT / n[0] : n[1];
-    pl.nyb = (n[1] + pl.TR - 1) / pl.TR;
+    pl.y1 = (pl.TR == 1 && !yper) ? 1 : 0;
+    pl.nyb = pl.y1 ? n[1] - 2 : (n[1] + pl.TR - 1) / pl.TR;
     pl.z0 = zper ? 0 : 1;
     pl.ntiles = pl.nyb * (zper ? n[2] : n[2] - 2);
     pl.JS = ((pl.TR + 2) * n[0] + 7) / 8 * 8;
