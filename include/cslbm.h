@@ -128,9 +128,9 @@ cslbm_status cslbm_set_jacobian(cslbm_ctx* ctx, const double* J9, int on_device)
 cslbm_status cslbm_update_metric(cslbm_ctx* ctx, const double* g6, const double* dg18,
                                  const double* Jnew9, int on_device);
 
-/* cslbm_update_metric with the metric derivatives dg18 [18][N] and the new
- * Jacobian Jnew9 [9][N] in FP32, the metric g6 [6][N] still in FP64 (its
- * inversion is FP64).  For FP32, FP16 and BF16 storage the library rounds
+/* The chart change of Sec. IV.B (cslbm_update_metric) with the metric
+ * derivatives dg18 [18][N] and the new Jacobian Jnew9 [9][N] in FP32, the
+ * metric g6 [6][N] still in FP64 (its inversion is FP64).  For FP32, FP16 and BF16 storage the library rounds
  * dg and J to FP32 before any use (Gamma and D phi are formed in FP32), so
  * the state this call leaves is bit for bit the one cslbm_update_metric
  * leaves with the same values in FP64; it lets a caller that uploads the
